@@ -1,0 +1,360 @@
+"""Pins for the oracle: what the paper and mathematics fix, checked without the oracle's
+own code path (hand values from Fig. 2, dense incidence products, numpy scatter routines,
+closed forms, invariants).  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sfgen
+from tests import npref
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig2.json")))
+
+
+def split(arr, off):
+    return [arr[off[p]:off[p + 1]].tolist() for p in range(len(off) - 1)]
+
+
+# ------------------------------------------------------------------ Fig. 2 worked example
+def test_fig2_layout():
+    ro, lo = oracle.layout(sfgen.fig2())
+    assert ro.tolist() == GOLD["rootoff"]
+    assert lo.tolist() == GOLD["leafoff"]
+
+
+def test_fig2_in_degree_and_reduce_sum():
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    deg = oracle.in_degree(f)
+    assert split(deg, ro) == GOLD["in_degree"]
+    root = oracle.reduce(f, "int32", 1, np.ones(lo[-1], np.int32), np.zeros(ro[-1], np.int32), "SUM")
+    assert split(root, ro) == GOLD["in_degree"]
+    rootf = oracle.reduce(f, "fp64", 1, np.ones(lo[-1]), np.zeros(ro[-1]), "SUM")
+    assert split(rootf.astype(int), ro) == GOLD["in_degree"]
+
+
+def test_fig2_bcast_replace():
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    x = np.concatenate([100 * p + np.arange(f.nroots[p]) for p in range(3)]).astype(np.int64)
+    leaf = oracle.bcast(f, "int64", 1, x, np.full(lo[-1], -1, np.int64), "REPLACE")
+    assert split(leaf, lo) == GOLD["bcast_replace"]["leaves"]
+
+
+def _fig2_leafvals(lo):
+    return np.concatenate([10 * q + np.arange(lo[q + 1] - lo[q]) for q in range(3)])
+
+
+def test_fig2_reduce_replace_last_edge_wins():
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    y = _fig2_leafvals(lo).astype(np.int32)
+    root = oracle.reduce(f, "int32", 1, y, np.full(ro[-1], -1, np.int32), "REPLACE")
+    assert split(root, ro) == GOLD["reduce_replace"]["roots"]
+
+
+def test_fig2_reduce_min():
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    y = _fig2_leafvals(lo).astype(np.float64)
+    root = oracle.reduce(f, "fp64", 1, y, np.full(ro[-1], 100.0), "MIN")
+    assert split(root.astype(int), ro) == GOLD["reduce_min"]["roots"]
+
+
+@pytest.mark.parametrize("dtype", ["int32", "int64", "fp64"])
+def test_fig2_fetch_and_op_multisf(dtype):
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    g = GOLD["fetch_and_op_sum"]
+    npt = oracle.NPTYPE[dtype]
+    r0 = np.concatenate([np.array(a) for a in g["root_init"]]).astype(npt)
+    root, upd = oracle.fetch_and_op(f, dtype, 1, r0, np.ones(lo[-1], npt), np.full(lo[-1], -7, npt), "SUM")
+    assert split(upd.astype(int), lo) == g["leafupdate"]
+    assert split(root.astype(int), ro) == g["roots"]
+
+
+# ------------------------------------------------------------------ dense incidence products
+FORESTS = [sfgen.random_forest(s, P, 9, 12) for s, P in [(1, 1), (2, 3), (3, 5), (4, 4), (5, 7), (6, 2)]]
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("bs", [1, 3])
+def test_bcast_is_incidence_product(f, bs):
+    Pm, L, R = npref.incidence(f)
+    nl, nr = Pm.shape
+    x = sfgen.data("fp64", nr * bs, 11, 1).reshape(nr, bs)
+    leaf0 = sfgen.data("fp64", nl * bs, 11, 2).reshape(nl, bs)
+    connected = Pm.sum(axis=1) > 0
+    got = oracle.bcast(f, "fp64", bs, x.ravel(), leaf0.ravel(), "REPLACE").reshape(nl, bs)
+    want = np.where(connected[:, None], Pm @ x, leaf0)
+    assert np.array_equal(got, want)
+    got = oracle.bcast(f, "fp64", bs, x.ravel(), leaf0.ravel(), "SUM").reshape(nl, bs)
+    want = leaf0 + Pm @ x       # one term per connected leaf: exact
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("bs", [1, 2])
+def test_reduce_sum_is_transpose_product_exact(f, bs):
+    """Integer-valued doubles: every partial sum is exact, so any order equals P^T y."""
+    Pm, L, R = npref.incidence(f)
+    nl, nr = Pm.shape
+    y = sfgen.data("int32", nl * bs, 12, 1).astype(np.float64).reshape(nl, bs)
+    r0 = sfgen.data("int32", nr * bs, 12, 2).astype(np.float64).reshape(nr, bs)
+    got = oracle.reduce(f, "fp64", bs, y.ravel(), r0.ravel(), "SUM").reshape(nr, bs)
+    assert np.array_equal(got, r0 + Pm.T @ y)
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_reduce_sum_fp_within_bound(f):
+    """Random doubles: |oracle - exact| <= (deg+1) u sum|.| (any summation order)."""
+    Pm, L, R = npref.incidence(f)
+    nl, nr = Pm.shape
+    y = sfgen.data("fp64", nl, 13, 1)
+    r0 = sfgen.data("fp64", nr, 13, 2)
+    got = oracle.reduce(f, "fp64", 1, y, r0, "SUM")
+    deg = Pm.sum(axis=0)
+    u = 2.0 ** -53
+    for r in range(nr):
+        terms = [r0[r]] + [y[l] for l in L[R == r]]
+        exact = math.fsum(terms)
+        assert abs(got[r] - exact) <= (deg[r] + 1) * u * sum(abs(t) for t in terms) + 1e-300
+
+
+def test_adjoint_identity_exact():
+    """<Bcast_REPLACE(x), y> = <x, Reduce_SUM(y)> over connected leaves (integers: exact)."""
+    for f in FORESTS:
+        Pm, L, R = npref.incidence(f)
+        nl, nr = Pm.shape
+        x = sfgen.data("int64", nr, 14, 1)
+        y = sfgen.data("int64", nl, 14, 2)
+        bx = oracle.bcast(f, "int64", 1, x, np.zeros(nl, np.int64), "REPLACE")
+        ry = oracle.reduce(f, "int64", 1, y, np.zeros(nr, np.int64), "SUM")
+        connected = Pm.sum(axis=1) > 0
+        assert int((bx * y * connected).sum()) == int((x * ry).sum())
+
+
+# ------------------------------------------------------------------ numpy scatter routines
+@pytest.mark.parametrize("f", FORESTS + [sfgen.cfg1_plain_tiny()], ids=lambda f: f.name)
+@pytest.mark.parametrize("dtype", ["int32", "int64", "fp32", "fp64"])
+def test_reduce_min_max_sum_match_numpy_scatter(f, dtype):
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    npt = oracle.NPTYPE[dtype]
+    kind = "wide" if dtype.startswith("int") else "signed"
+    y = sfgen.data(dtype, lo[-1] * 2, 15, 1, kind).reshape(-1, 2)
+    r0 = sfgen.data(dtype, ro[-1] * 2, 15, 2, kind).reshape(-1, 2)
+    for op, ufunc in (("MIN", np.minimum), ("MAX", np.maximum)):
+        want = r0.copy()
+        ufunc.at(want, R, y[L])
+        got = oracle.reduce(f, dtype, 2, y.ravel(), r0.ravel(), op).reshape(-1, 2)
+        assert np.array_equal(got, want), op
+    if dtype.startswith("int"):   # wraparound sum: numpy add.at wraps too
+        want = r0.copy()
+        with np.errstate(over="ignore"):
+            np.add.at(want, R, y[L])
+        got = oracle.reduce(f, dtype, 2, y.ravel(), r0.ravel(), "SUM").reshape(-1, 2)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
+def test_bcast_ops_match_numpy_gather(f, op):
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    x = sfgen.data("int32", ro[-1], 16, 1, "wide")
+    leaf0 = sfgen.data("int32", lo[-1], 16, 2, "wide")
+    want = leaf0.copy()
+    with np.errstate(over="ignore"):
+        want[L] = {"SUM": np.add, "MIN": np.minimum, "MAX": np.maximum}[op](leaf0[L], x[R])
+    assert np.array_equal(oracle.bcast(f, "int32", 1, x, leaf0, op), want)
+
+
+def test_reduce_replace_last_edge_matches_numpy():
+    for f in FORESTS:
+        L, R = npref.edge_arrays(f)
+        ro, lo = npref.offsets(f)
+        y = sfgen.data("int64", lo[-1], 17, 1, "wide")
+        r0 = sfgen.data("int64", ro[-1], 17, 2, "wide")
+        last = np.full(ro[-1], -1, np.int64)
+        np.maximum.at(last, R, np.arange(len(R)))      # last canonical edge of every root
+        want = r0.copy()
+        hit = last >= 0
+        want[hit] = y[L[last[hit]]]
+        assert np.array_equal(oracle.reduce(f, "int64", 1, y, r0, "REPLACE"), want)
+
+
+def test_round_trip_one_to_one():
+    """Ping-pong (Sec. VI.A): Reduce REPLACE after Bcast REPLACE restores the roots."""
+    for f in [sfgen.one_to_one(s, P, n) for s, P, n in [(1, 1, 7), (2, 3, 50), (3, 8, 33)]] + [sfgen.pingpong(100)]:
+        ro, lo = oracle.layout(f)
+        x = sfgen.data("fp64", ro[-1] * 3, 18, 1)
+        leaf = oracle.bcast(f, "fp64", 3, x, np.zeros(lo[-1] * 3), "REPLACE")
+        back = oracle.reduce(f, "fp64", 3, leaf, np.zeros(ro[-1] * 3), "REPLACE")
+        assert np.array_equal(back, x)
+
+
+# ------------------------------------------------------------------ blocked fold D (hand values)
+def star(n):
+    """One root on rank 0, n leaves on rank 0 all pointing at it."""
+    return sfgen.Forest(1, np.array([1]), np.array([n]), [None], [np.zeros(n, np.int32)],
+                        [np.zeros(n, np.int64)], name=f"star{n}")
+
+
+def test_fold_left_order_fp64():
+    """Leaves (1, 1e16, -1e16): the left fold gives (1+1e16)-1e16 = 0 (1 is absorbed),
+    any order that adds 1e16 and -1e16 first gives 1."""
+    f = star(3)
+    got = oracle.reduce(f, "fp64", 1, np.array([1.0, 1e16, -1e16]), np.array([0.0]), "SUM")
+    assert got[0] == 0.0
+    got = oracle.reduce(f, "fp64", 1, np.array([1e16, -1e16, 1.0]), np.array([0.0]), "SUM")
+    assert got[0] == 1.0
+
+
+def test_fold_root_added_last():
+    """root + D(y), not ((root + y0) + y1): root 2^53, leaves 1, 1 -> D = 2 -> 2^53 + 2 exactly;
+    adding the root first would absorb both ones (ties to even) and give 2^53."""
+    f = star(2)
+    got = oracle.reduce(f, "fp64", 1, np.array([1.0, 1.0]), np.array([2.0 ** 53]), "SUM")
+    assert got[0] == 2.0 ** 53 + 2.0
+
+
+def test_fold_blocks_of_64_fp32():
+    """128 leaves: 2^24 then 127 ones (fp32).  Block 0 = fl(2^24 + 1 + ...) = 2^24 (each 1 is
+    a tie rounded to even), block 1 = 64 exactly; D = 2^24 + 64.  A plain left fold would
+    give 2^24, a block of 32 would give 2^24 + 96."""
+    f = star(128)
+    y = np.ones(128, np.float32)
+    y[0] = 2.0 ** 24
+    got = oracle.reduce(f, "fp32", 1, y, np.zeros(1, np.float32), "SUM")
+    assert got[0] == np.float32(2.0 ** 24 + 64)
+
+
+def test_fold_three_levels_fp32():
+    """4097 leaves: 2^24 then 4096 ones.  Level 1: 65 blocks -> (2^24, 64 x 63, 1).  Level 2:
+    65 > 64 so blocks again -> (2^24 + 4032, 1).  Level 3: 2^24 + 4033 is a tie between
+    2^24 + 4032 (even significand) and 2^24 + 4034 -> 2^24 + 4032."""
+    f = star(4097)
+    y = np.ones(4097, np.float32)
+    y[0] = 2.0 ** 24
+    got = oracle.reduce(f, "fp32", 1, y, np.zeros(1, np.float32), "SUM")
+    assert got[0] == np.float32(2.0 ** 24 + 4032)
+
+
+def test_fold_bf16_accumulates_in_fp32_and_rounds_once():
+    """bf16 leaves 1.0 x 300 into root 0: fp32 sum is 300 exactly; bf16(300) = 300 (needs 7
+    significand bits: 300 = 0b100101100).  Rounding after every add would stall at 256."""
+    f = star(300)
+    one = np.array([0x3F80] * 300, np.uint16)
+    got = oracle.reduce(f, "bf16", 1, one, np.zeros(1, np.uint16), "SUM")
+    val = np.array([int(got[0]) << 16], np.uint32).view(np.float32)[0]
+    assert val == 300.0
+
+
+# ------------------------------------------------------------------ FetchAndOp invariants
+@pytest.mark.parametrize("f", FORESTS + [sfgen.cfg1_plain_tiny()], ids=lambda f: f.name)
+def test_fetch_and_op_multisf_invariant(f):
+    """Roots at degree-prefix offsets, leaves 1 (Sec. III.B): each root's fetched values are
+    exactly {o, ..., o+deg-1}, increasing in canonical order, and the root ends at o+deg."""
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    deg = np.bincount(R, minlength=ro[-1])
+    off = np.concatenate([[0], np.cumsum(deg)[:-1]]).astype(np.int32)
+    root, upd = oracle.fetch_and_op(f, "int32", 1, off, np.ones(lo[-1], np.int32),
+                                    np.full(lo[-1], -1, np.int32), "SUM")
+    assert np.array_equal(root, off + deg)
+    order = np.argsort(R, kind="stable")          # edges grouped by root, canonical inside
+    fetched = upd[L[order]]
+    assert np.array_equal(fetched, np.arange(len(L)))
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_fetch_and_op_prefix_sums_match_cumsum(f):
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = sfgen.data("int64", lo[-1], 19, 1, "wide")
+    r0 = sfgen.data("int64", ro[-1], 19, 2, "wide")
+    root, upd = oracle.fetch_and_op(f, "int64", 1, r0, y, np.zeros(lo[-1], np.int64), "SUM")
+    want_root, want_upd = r0.copy(), np.zeros(lo[-1], np.int64)
+    with np.errstate(over="ignore"):
+        for r in np.unique(R):
+            es = np.nonzero(R == r)[0]
+            inc = np.cumsum(np.concatenate([[r0[r]], y[L[es]]]).astype(np.int64))
+            want_upd[L[es]] = inc[:-1]
+            want_root[r] = inc[-1]
+    assert np.array_equal(root, want_root)
+    assert np.array_equal(upd, want_upd)
+
+
+def test_fetch_and_op_replace_is_a_chain_of_swaps():
+    f = star(4)
+    root, upd = oracle.fetch_and_op(f, "int32", 1, np.array([9], np.int32),
+                                    np.array([1, 2, 3, 4], np.int32), np.zeros(4, np.int32), "REPLACE")
+    assert root.tolist() == [4] and upd.tolist() == [9, 1, 2, 3]
+
+
+def test_fetch_and_op_max_fetches_running_max():
+    f = star(5)
+    root, upd = oracle.fetch_and_op(f, "fp64", 1, np.array([0.5]), np.array([0.1, 0.9, 0.3, 1.5, -2.0]),
+                                    np.zeros(5), "MAX")
+    assert root.tolist() == [1.5] and upd.tolist() == [0.5, 0.5, 0.9, 0.9, 1.5]
+
+
+# ------------------------------------------------------------------ helpers of the oracle
+def test_bf16_rounding_matches_torch_cpu():
+    torch = pytest.importorskip("torch")
+    bits = sfgen.rng.u64(99, 1, 200000) >> np.uint64(32)
+    x = bits.astype(np.uint32).view(np.float32)
+    x = x[np.isfinite(x)]
+    # ties and near-ties explicitly
+    base = np.arange(0, 1 << 16, dtype=np.uint32) << np.uint32(16)
+    extra = np.concatenate([base | 0x8000, base | 0x7FFF, base | 0x8001]).view(np.float32)
+    x = np.concatenate([x, extra[np.isfinite(extra)]])
+    want = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    got = oracle.f32_to_bf16(x)
+    assert np.array_equal(got, want)
+
+
+def test_sum_reference_matches_fsum():
+    f = sfgen.random_forest(21, 3, 6, 40)
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = sfgen.data("fp64", lo[-1], 20, 1) * 1e3
+    r0 = sfgen.data("fp64", ro[-1], 20, 2)
+    s, a = oracle.sum_reference(f, "fp64", 1, y, r0)
+    for r in range(ro[-1]):
+        terms = [r0[r]] + list(y[L[R == r]])
+        ex = math.fsum(terms)
+        assert abs(s[r] - ex) <= 4 * 2.0 ** -53 * abs(ex) + 1e-290
+        assert a[r] == pytest.approx(sum(abs(t) for t in terms), rel=1e-12)
+
+
+def test_maxloc_matches_lexsort():
+    f = sfgen.random_forest(22, 4, 8, 30)
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = sfgen.data("int32", lo[-1], 21, 1)     # many ties (values < 1000, few edges)
+    y[::3] = 5
+    val, arg = oracle.reduce_maxloc(f, "int32", 1, y)
+    e = np.arange(len(L))
+    order = np.lexsort((e, -y[L].astype(np.int64), R))      # by root, value desc, edge asc
+    first = np.ones(len(order), bool)
+    first[1:] = R[order][1:] != R[order][:-1]
+    want_val = np.zeros(ro[-1], np.int32)
+    want_arg = np.full(ro[-1], -1, np.int64)
+    want_val[R[order][first]] = y[L][order][first]
+    want_arg[R[order][first]] = e[order][first]
+    assert np.array_equal(val, want_val) and np.array_equal(arg, want_arg)
+
+
+def test_empty_forest_and_isolated():
+    f = sfgen.Forest(2, np.array([3, 0]), np.array([0, 0]), [None, None],
+                     [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int64)] * 2)
+    ro, lo = oracle.layout(f)
+    assert ro.tolist() == [0, 3, 3] and lo.tolist() == [0, 0, 0]
+    r = oracle.reduce(f, "fp64", 1, np.zeros(0), np.array([1.0, 2.0, 3.0]), "SUM")
+    assert r.tolist() == [1.0, 2.0, 3.0]
