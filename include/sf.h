@@ -1,0 +1,213 @@
+/* sf.h -- C ABI of libsfgb, star-forest communication on one GB300 GPU.
+ *
+ * A star forest (Sec. III.A) is a set of disjoint stars: each root has zero or more leaves,
+ * each leaf at most one root.  The graph is described per simulated rank p by the owner of
+ * the leaves: nroots[p] roots, nleaves[p] connected leaves with local indices ilocal[p]
+ * (NULL = 0..nleaves[p]-1) and their root addresses iremote[p][i] = (rank, index).
+ * All ranks live in one GPU's memory.  Their data sits back to back, rank-major:
+ *   rootdata unit rootoff[p] + r  is root r of rank p,   rootoff[p] = sum_{p'<p} nroots[p']
+ *   leafdata unit leafoff[q] + l  is leaf l of rank q,   leafoff[q] = sum_{q'<q} extent[q']
+ * where a rank's leaf extent is max(ilocal[q])+1, or nleaves[q] when ilocal[q] is NULL.
+ * A unit is bs consecutive elements of one dtype (the MPI datatype "unit" of Sec. III.B).
+ * Edge e = (q, i) is the i-th leaf rank q describes; canonical edge order is ascending (q, i).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int error code, SF_SUCCESS (0) on success (Sec. III.A: all
+ *    PetscSF routines return an error code).  Nothing aborts or throws across the ABI.
+ *  - Graph arrays are copied by sf_create and stay owned by the caller.
+ *  - rootdata / leafdata / leafupdate are device pointers owned by the caller, except in the
+ *    *_with_memtype calls.  They must be aligned to the element size of the unit's dtype.
+ *  - sf_stream_t is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *    Every operation is enqueued on that stream in order, with no host synchronisation.
+ *    Results are valid on that stream after the matching End (Sec. III.B: begin/end take
+ *    the same arguments; buffers must not change between them).
+ *  - Leaves not listed in ilocal and roots without leaves are never written.
+ *  - Calls on one sf_t are not thread safe; different sf_t may be used concurrently.
+ */
+#ifndef SFGB_SF_H
+#define SFGB_SF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_s sf_t;
+typedef struct sf_batch_s sf_batch_t;
+typedef void *sf_stream_t;
+
+/* Root address of a leaf: PetscSFNode {rank, offset} of Sec. III.A. */
+typedef struct {
+  int32_t rank;
+  int64_t index;
+} sf_node;
+
+/* Element types of a unit. */
+enum { SF_INT32 = 0, SF_INT64 = 1, SF_FP32 = 2, SF_FP64 = 3, SF_BF16 = 4 };
+
+/* A unit: bs consecutive elements of dtype (bs >= 1). */
+typedef struct {
+  int32_t dtype;
+  int32_t bs;
+} sf_unit;
+
+/* Reduction operators of Sec. III.B (MPI_REPLACE, MPI_SUM, MPI_MIN, MPI_MAX). */
+enum { SF_REPLACE = 0, SF_SUM = 1, SF_MIN = 2, SF_MAX = 3 };
+
+/* How Reduce combines several leaves of one root (Sec. V.C uses atomics on duplicates).
+ * DETERMINISTIC: each root combines its leaves in canonical edge order; a floating point SUM
+ *   adds the blocked left fold D of the leaf values (block SF_FOLD_BLOCK, see below) to the
+ *   root; bit-identical from run to run.
+ * ATOMIC: device atomics in whatever order the hardware applies them.
+ * AUTO: the library picks (currently DETERMINISTIC, or what sf_autotune measured fastest).
+ * Reduce REPLACE always takes the value of the root's last leaf in canonical order;
+ * bf16 SUM always accumulates in fp32 deterministically and rounds once. */
+enum { SF_MODE_AUTO = 0, SF_MODE_ATOMIC = 1, SF_MODE_DETERMINISTIC = 2 };
+
+/* Blocked fold D(y_0..y_{n-1}): if n <= SF_FOLD_BLOCK, ((y_0 + y_1) + ...) + y_{n-1};
+ * otherwise D of the list of left folds of consecutive blocks of SF_FOLD_BLOCK values. */
+#define SF_FOLD_BLOCK 64
+
+/* Data paths for Bcast (Sec. V.B):
+ * FUSED: one scatter kernel per operation, leafdata[leaf] op= rootdata[root] for every edge,
+ *   grouped by (root rank, leaf rank) with self first; index-free on detected patterns.
+ * THREE_PHASE: pack remote edges into a root buffer, move each (root rank -> leaf rank) chunk
+ *   into a leaf buffer, unpack into leafdata; self edges are scattered directly.
+ * ROOT_MAJOR: each root unit is read once and written to all of its leaves.
+ * AUTO: the library picks (FUSED, or what sf_autotune measured fastest). */
+enum { SF_PATH_AUTO = 0, SF_PATH_FUSED = 1, SF_PATH_THREE_PHASE = 2, SF_PATH_ROOT_MAJOR = 3 };
+
+/* Where data lives, for the *_with_memtype calls (PetscSFBcastWithMemTypeBegin, Sec. V.C). */
+enum { SF_MEM_HOST = 0, SF_MEM_DEVICE = 1 };
+
+/* Error codes. */
+enum {
+  SF_SUCCESS = 0,
+  SF_ERR_ARG = 1,          /* invalid argument (size, dtype, bs, op, mode, memtype) */
+  SF_ERR_NULL = 2,         /* required pointer is NULL */
+  SF_ERR_RANGE = 3,        /* iremote rank/index or ilocal out of range */
+  SF_ERR_DUP_LEAF = 4,     /* a rank lists the same local leaf twice (stars must be disjoint) */
+  SF_ERR_STATE = 5,        /* call out of order (e.g. operation before sf_setup) */
+  SF_ERR_NO_PENDING = 6,   /* End without a matching Begin */
+  SF_ERR_PENDING = 7,      /* Begin already pending with these arguments, or destroy with one */
+  SF_ERR_UNSUPPORTED = 8,  /* valid but not supported (e.g. atomic FetchAndOp with bs > 1) */
+  SF_ERR_ALLOC = 9,        /* host or device allocation failed */
+  SF_ERR_CUDA = 10,        /* a CUDA runtime call failed (no device, launch failure, ...) */
+  SF_ERR_ALIGN = 11,       /* data pointer not aligned to the element size */
+  SF_ERR_TOO_LARGE = 12    /* sizes beyond what the library indexes (2^31-1 units) */
+};
+
+/* Statistics of the setup pass (Sec. V.A-B), valid after sf_analyze or sf_setup. */
+typedef struct {
+  int32_t nranks;
+  int32_t analyzed;
+  int32_t setup_done;
+  int32_t has_dup_roots;       /* some root has in-degree > 1 (Sec. V.C) */
+  int64_t nroots_total;        /* rootoff[nranks] */
+  int64_t leaf_extent_total;   /* leafoff[nranks] */
+  int64_t nedges;
+  int64_t max_in_degree;
+  int64_t connected_roots;     /* roots with in-degree >= 1 */
+  int64_t multi_roots;         /* roots with in-degree >= 2 */
+  int64_t multi_edges;         /* edges into those roots */
+  int64_t segments;            /* non-empty (root rank, leaf rank) pairs */
+  int64_t self_edges;          /* edges whose root and leaf rank agree */
+  int64_t runs;                /* runs of the (root rank, leaf rank) edge order */
+  int64_t runs_pattern;        /* runs with both sides index-free (contiguous / 3-D) */
+  int64_t runs_3d;             /* of those, with more than one row */
+  int64_t edges_both_pattern;  /* edges with no index load on either side */
+  int64_t edges_one_indexed;   /* edges with exactly one side index-driven */
+  int64_t edges_two_indexed;   /* edges with both sides index-driven */
+  int64_t rm_masked_runs;      /* root-major plan: contiguous single-leaf runs */
+  int64_t rm_masked_edges;
+  int64_t rm_pairs;            /* root-major plan: other single-leaf roots */
+  int64_t rm_chunks;           /* root-major plan: blocks of SF_FOLD_BLOCK leaves of multi roots */
+  int64_t device_plan_bytes;   /* device memory held by the plans */
+} sf_info;
+
+/* Create a star forest (PetscSFCreate + PetscSFSetGraph, Sec. III.A).
+ * nranks >= 1; nroots[p], nleaves[p] >= 0; ilocal may be NULL (all ranks contiguous) and
+ * ilocal[p] may be NULL; iremote[p] may be NULL only when nleaves[p] == 0.  The arrays are
+ * validated (ranges, duplicate leaves) and copied.  *out receives the handle.
+ * Errors: SF_ERR_NULL, SF_ERR_ARG, SF_ERR_RANGE, SF_ERR_DUP_LEAF, SF_ERR_TOO_LARGE, SF_ERR_ALLOC. */
+int sf_create(int32_t nranks, const int64_t nroots[], const int64_t nleaves[],
+              const int64_t *const ilocal[], const sf_node *const iremote[], sf_t **out);
+
+/* Host part of PetscSFSetUp (Sec. V.A-B): two-sided grouping by (root rank, leaf rank) with
+ * self first, pattern detection (contiguous and multi-strided 3-D runs), duplicate-root
+ * detection, root-major plan.  Needs no GPU.  Idempotent. */
+int sf_analyze(sf_t *sf);
+
+/* PetscSFSetUp (Sec. III.A): sf_analyze if not done, then upload the plans to the current
+ * CUDA device and allocate the persistent buffers.  Enqueued on `stream`; synchronises it
+ * once before returning.  Errors: SF_ERR_CUDA, SF_ERR_ALLOC. */
+int sf_setup(sf_t *sf, sf_stream_t stream);
+
+/* rootoff[nranks+1] and leafoff[nranks+1] of the concatenated buffers (caller-allocated). */
+int sf_get_layout(const sf_t *sf, int64_t *rootoff, int64_t *leafoff);
+
+int sf_get_info(const sf_t *sf, sf_info *info);
+
+/* Select the Reduce mode (SF_MODE_*) and the Bcast data path (SF_PATH_*). */
+int sf_set_mode(sf_t *sf, int32_t mode);
+int sf_set_path(sf_t *sf, int32_t path);
+
+/* Bcast (Sec. III.B): for every edge, leafdata[leaf] = op(leafdata[leaf], rootdata[root]).
+ * Begin enqueues the work on `stream` (all of it for FUSED/ROOT_MAJOR; pack, self scatter and
+ * move for THREE_PHASE); End enqueues what remains (the unpack) and must repeat the arguments.
+ * rootdata must not alias leafdata.  Errors: SF_ERR_STATE, SF_ERR_ARG, SF_ERR_NULL,
+ * SF_ERR_ALIGN, SF_ERR_PENDING, SF_ERR_NO_PENDING, SF_ERR_CUDA. */
+int sf_bcast_begin(sf_t *sf, sf_unit unit, const void *rootdata, void *leafdata, int32_t op,
+                   sf_stream_t stream);
+int sf_bcast_end(sf_t *sf, sf_unit unit, const void *rootdata, void *leafdata, int32_t op,
+                 sf_stream_t stream);
+
+/* Reduce (Sec. III.B): for every edge, rootdata[root] = op(rootdata[root], leafdata[leaf]),
+ * combined per root as the mode says (see SF_MODE_*).  Same begin/end rules as Bcast. */
+int sf_reduce_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                    sf_stream_t stream);
+int sf_reduce_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                  sf_stream_t stream);
+
+/* FetchAndOp (Sec. III.B): for each root, its leaves are applied one at a time; before leaf
+ * e is applied, the root's current value is stored into leafupdate[leaf e]:
+ *   leafupdate[leaf] = rootdata[root];  rootdata[root] = op(rootdata[root], leafdata[leaf]).
+ * DETERMINISTIC (and AUTO) mode applies a root's leaves in canonical edge order; ATOMIC mode
+ * in hardware order (bs must be 1, else SF_ERR_UNSUPPORTED).  leafupdate must not alias
+ * leafdata or rootdata. */
+int sf_fetch_and_op_begin(sf_t *sf, sf_unit unit, void *rootdata, const void *leafdata,
+                          void *leafupdate, int32_t op, sf_stream_t stream);
+int sf_fetch_and_op_end(sf_t *sf, sf_unit unit, void *rootdata, const void *leafdata,
+                        void *leafupdate, int32_t op, sf_stream_t stream);
+
+/* Bcast/Reduce with explicit memory types (PetscSFBcastWithMemTypeBegin, Sec. V.C):
+ * rootmtype / leafmtype are SF_MEM_HOST or SF_MEM_DEVICE.  Host buffers are staged through
+ * library-owned device buffers: inputs are copied host->device at Begin, the output is
+ * copied device->host at End, all on `stream`.  Host memory should be page-locked for the
+ * copies to be asynchronous; pageable memory works but the copies then block the host.
+ * The host output is valid once `stream` has completed after End. */
+int sf_bcast_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t rootmtype, const void *rootdata,
+                                int32_t leafmtype, void *leafdata, int32_t op, sf_stream_t stream);
+int sf_bcast_with_memtype_end(sf_t *sf, sf_unit unit, int32_t rootmtype, const void *rootdata,
+                              int32_t leafmtype, void *leafdata, int32_t op, sf_stream_t stream);
+int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
+                                 int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
+int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
+                               int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
+
+/* Free the forest and its device plans.  SF_ERR_PENDING (and nothing freed) if a Begin has
+ * no End yet.  Synchronises the device work the library enqueued before freeing. */
+int sf_destroy(sf_t *sf);
+
+/* Static description of an error code (never NULL). */
+const char *sf_error_string(int code);
+
+/* Kernels launched by the library since the process started (all entry points). */
+int64_t sf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFGB_SF_H */

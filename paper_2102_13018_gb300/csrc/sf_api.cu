@@ -1,0 +1,615 @@
+// sf_api.cu -- the C ABI of sf.h: object lifetime, device plans, begin/end bookkeeping and
+// dispatch of every operation to the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sf.h"
+#include "sf_host.h"
+#include "sf_launch.h"
+
+using namespace sfgb;
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+
+enum { K_BCAST = 1, K_REDUCE = 2, K_FETCH = 3, K_BCAST_MT = 4, K_REDUCE_MT = 5 };
+
+struct Pending {
+  int kind;
+  sf_unit unit;
+  const void *p0, *p1, *p2;
+  int32_t op;
+  int32_t m0, m1;      // memtypes (memtype calls)
+  int32_t finish;      // work left for End: 0 none, 1 three-phase unpack
+};
+
+int elem_size(int dtype) {
+  switch (dtype) {
+    case SF_INT32: case SF_FP32: return 4;
+    case SF_INT64: case SF_FP64: return 8;
+    case SF_BF16: return 2;
+  }
+  return 0;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sf_s {
+  Graph g;
+  HostPlan hp;
+  sf_info info{};
+  bool setup = false;
+  int device = -1;
+  DevBuf blob;                 // all plan arrays
+  DevPlan dp{};
+  std::vector<Tile> h_move_tiles;
+  const Tile *move_tiles = nullptr;
+  int32_t n_move_tiles = 0;
+  DevBuf partial, counter;     // fold scratch
+  DevBuf rootbuf, leafbuf;     // three-phase buffers
+  DevBuf stage_root, stage_leaf;   // memtype staging
+  int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
+  std::vector<Pending> pending;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? SF_SUCCESS : SF_ERR_CUDA; }
+
+// grow-only device buffer; a reallocation waits for the device so no kernel still uses the old one
+int ensure(DevBuf &b, size_t bytes, bool zero, cudaStream_t s) {
+  if (bytes == 0 || b.bytes >= bytes) return SF_SUCCESS;
+  if (b.p) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ERR_CUDA;
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_ALLOC;
+  }
+  b.bytes = bytes;
+  if (zero && cudaMemsetAsync(b.p, 0, bytes, s) != cudaSuccess) return SF_ERR_CUDA;
+  return SF_SUCCESS;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// Layout of the plan blob: each array 256-byte aligned.
+struct BlobBuilder {
+  std::vector<char> host;
+  template <typename V> size_t add(const std::vector<V> &v) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + v.size() * sizeof(V));
+    if (!v.empty()) memcpy(host.data() + off, v.data(), v.size() * sizeof(V));
+    return off;
+  }
+};
+
+// widest vector (bytes) usable for a unit of `ub` bytes with the given pointers
+int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs) {
+  static const int cand[] = {16, 8, 4, 2};
+  for (int vb : cand) {
+    if (vb < w || ub % vb) continue;
+    if (vb != w && !allow_wide) continue;
+    bool ok = true;
+    for (const void *p : ptrs)
+      if (p && (reinterpret_cast<uintptr_t>(p) % vb)) ok = false;
+    if (ok) return vb;
+  }
+  return 0;
+}
+
+int check_unit(const sf_unit &u, int32_t op) {
+  if (elem_size(u.dtype) == 0 || u.bs < 1 || u.bs > (1 << 20)) return SF_ERR_ARG;
+  if (op < SF_REPLACE || op > SF_MAX) return SF_ERR_ARG;
+  return SF_SUCCESS;
+}
+
+int check_ptr(const void *p, int w) {
+  if (!p) return SF_ERR_NULL;
+  if (reinterpret_cast<uintptr_t>(p) % w) return SF_ERR_ALIGN;
+  return SF_SUCCESS;
+}
+
+Pending *find_pending(sf_t *sf, int kind, const sf_unit &u, const void *p0, const void *p1, const void *p2,
+                      int32_t op, int32_t m0, int32_t m1) {
+  for (auto &pd : sf->pending)
+    if (pd.kind == kind && pd.unit.dtype == u.dtype && pd.unit.bs == u.bs && pd.p0 == p0 && pd.p1 == p1 &&
+        pd.p2 == p2 && pd.op == op && pd.m0 == m0 && pd.m1 == m1)
+      return &pd;
+  return nullptr;
+}
+
+void drop_pending(sf_t *sf, Pending *pd) { sf->pending.erase(sf->pending.begin() + (pd - sf->pending.data())); }
+
+int launched(cudaError_t e) {
+  if (e != cudaSuccess) return SF_ERR_CUDA;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return SF_SUCCESS;
+}
+
+TsArgs ts_args(const sf_t *sf, const Tile *tiles, const void *src, void *dst, void *upd, int nv, int phase) {
+  TsArgs a{};
+  a.runs = sf->dp.runs;
+  a.ridx = sf->dp.ts_ridx;
+  a.lidx = sf->dp.ts_lidx;
+  a.tiles = tiles;
+  a.src = src;
+  a.dst = dst;
+  a.upd = upd;
+  a.nv = nv;
+  a.phase = phase;
+  return a;
+}
+
+RmArgs rm_args(sf_t *sf, const Tile *tiles, void *root, void *leaf, void *upd, int nv) {
+  RmArgs a{};
+  a.mruns = sf->dp.mruns;
+  a.mask = sf->dp.mask;
+  a.pr_root = sf->dp.pr_root;
+  a.pr_leaf = sf->dp.pr_leaf;
+  a.m_root = sf->dp.m_root;
+  a.m_ptr = sf->dp.m_ptr;
+  a.m_leaf = sf->dp.m_leaf;
+  a.m_slot = sf->dp.m_slot;
+  a.m_ctr = sf->dp.m_ctr;
+  a.ch_m = sf->dp.ch_m;
+  a.ch_e0 = sf->dp.ch_e0;
+  a.tiles = tiles;
+  a.root = root;
+  a.leaf = leaf;
+  a.upd = upd;
+  a.partial = sf->partial.p;
+  a.counter = static_cast<int32_t *>(sf->counter.p);
+  a.nv = nv;
+  return a;
+}
+
+// ---- Bcast data paths -------------------------------------------------------------------
+int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s,
+                 int path, int *finish) {
+  const int w = elem_size(u.dtype), ub = w * u.bs;
+  *finish = 0;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  const bool copy = op == SF_REPLACE;
+  if (path == SF_PATH_ROOT_MAJOR) {
+    const int vb = pick_vb(w, ub, true, {root, leaf});
+    if (!vb) return SF_ERR_ALIGN;
+    RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vb);
+    return launched(launch_rm(u.dtype, op, vb, RM_BCAST, a, sf->dp.n_rm_fold_tiles, s));
+  }
+  if (path == SF_PATH_THREE_PHASE && sf->dp.remote_units > 0) {
+    const size_t bytes = size_t(sf->dp.remote_units) * ub;
+    int rc;
+    if ((rc = ensure(sf->rootbuf, bytes, false, s)) || (rc = ensure(sf->leafbuf, bytes, false, s))) return rc;
+    const int vb = pick_vb(w, ub, copy, {root, leaf, sf->rootbuf.p, sf->leafbuf.p});
+    if (!vb) return SF_ERR_ALIGN;
+    const int nv = ub / vb;
+    // self edges: direct scatter; remote edges: pack, then move
+    TsArgs self = ts_args(sf, sf->dp.ts_self_tiles, root, leaf, nullptr, nv, PH_FUSED);
+    if ((rc = launched(launch_ts(u.dtype, op, vb, false, false, false, self, sf->dp.n_ts_self_tiles, s)))) return rc;
+    const int vbc = pick_vb(w, ub, true, {root, sf->rootbuf.p, sf->leafbuf.p});
+    TsArgs pack = ts_args(sf, sf->dp.ts_remote_tiles, root, sf->rootbuf.p, nullptr, ub / vbc, PH_PACK);
+    if ((rc = launched(launch_ts(u.dtype, SF_REPLACE, vbc, false, false, false, pack, sf->dp.n_ts_remote_tiles, s))))
+      return rc;
+    MoveArgs mv{sf->dp.segs, sf->move_tiles, sf->rootbuf.p, sf->leafbuf.p, ub / vbc, 0};
+    if ((rc = launched(launch_move(vbc, mv, sf->n_move_tiles, s)))) return rc;
+    *finish = 1;
+    return SF_SUCCESS;
+  }
+  const int vb = pick_vb(w, ub, true, {root, leaf});
+  if (!vb) return SF_ERR_ALIGN;
+  const int vbo = copy ? vb : (vb == 16 ? 16 : w);
+  TsArgs a = ts_args(sf, sf->dp.ts_tiles, root, leaf, nullptr, ub / vbo, PH_FUSED);
+  return launched(launch_ts(u.dtype, op, vbo, false, false, false, a, sf->dp.n_ts_tiles, s));
+}
+
+int bcast_finish(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s) {
+  const int w = elem_size(u.dtype), ub = w * u.bs;
+  const int vb = pick_vb(w, ub, op == SF_REPLACE, {leaf, sf->leafbuf.p});
+  if (!vb) return SF_ERR_ALIGN;
+  const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+  TsArgs a = ts_args(sf, sf->dp.ts_remote_tiles, sf->leafbuf.p, leaf, nullptr, ub / vbo, PH_UNPACK);
+  return launched(launch_ts(u.dtype, op, vbo, false, false, false, a, sf->dp.n_ts_remote_tiles, s));
+}
+
+// ---- Reduce -------------------------------------------------------------------------------
+int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s) {
+  const int w = elem_size(u.dtype), ub = w * u.bs;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  const bool atomic = sf->mode == SF_MODE_ATOMIC && op != SF_REPLACE && u.dtype != SF_BF16;
+  if (atomic) {
+    TsArgs a = ts_args(sf, sf->dp.ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
+    return launched(launch_ts(u.dtype, op, w, true, true, false, a, sf->dp.n_ts_tiles, s));
+  }
+  const int vb = pick_vb(w, ub, true, {root, leaf});
+  if (!vb) return SF_ERR_ALIGN;
+  const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+  const int nv = ub / vbo;
+  int rc;
+  if (op != SF_REPLACE && sf->dp.n_partial_slots > 0) {
+    const size_t pbytes = size_t(sf->dp.n_partial_slots) * nv * acc_pack_bytes(u.dtype, op, vbo);
+    const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
+    if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
+  }
+  const Tile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+  RmArgs a = rm_args(sf, tiles, root, const_cast<void *>(leaf), nullptr, nv);
+  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, a, nt, s));
+}
+
+// ---- FetchAndOp ---------------------------------------------------------------------------
+int fetch_launch(sf_t *sf, const sf_unit &u, void *root, const void *leaf, void *upd, int32_t op, cudaStream_t s) {
+  const int w = elem_size(u.dtype), ub = w * u.bs;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  if (sf->mode == SF_MODE_ATOMIC) {
+    if (u.bs != 1) return SF_ERR_UNSUPPORTED;
+    TsArgs a = ts_args(sf, sf->dp.ts_tiles, leaf, root, upd, 1, PH_FUSED);
+    return launched(launch_ts(u.dtype, op, w, true, true, true, a, sf->dp.n_ts_tiles, s));
+  }
+  const int vb = pick_vb(w, ub, true, {root, leaf, upd});
+  if (!vb) return SF_ERR_ALIGN;
+  const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+  RmArgs a = rm_args(sf, sf->dp.rm_fetch_tiles, root, const_cast<void *>(leaf), upd, ub / vbo);
+  return launched(launch_rm(u.dtype, op, vbo, RM_FETCH, a, sf->dp.n_rm_fetch_tiles, s));
+}
+
+int bcast_path(const sf_t *sf) { return sf->path == SF_PATH_AUTO ? SF_PATH_FUSED : sf->path; }
+
+int ensure_ready(const sf_t *sf) {
+  if (!sf) return SF_ERR_NULL;
+  if (!sf->setup) return SF_ERR_STATE;
+  return SF_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sf_create(int32_t nranks, const int64_t nroots[], const int64_t nleaves[], const int64_t *const ilocal[],
+              const sf_node *const iremote[], sf_t **out) {
+  if (!out) return SF_ERR_NULL;
+  *out = nullptr;
+  sf_t *sf = new (std::nothrow) sf_t();
+  if (!sf) return SF_ERR_ALLOC;
+  const int rc = build_graph(nranks, nroots, nleaves, ilocal, iremote, sf->g);
+  if (rc != SF_SUCCESS) {
+    delete sf;
+    return rc;
+  }
+  sf->info.nranks = nranks;
+  *out = sf;
+  return SF_SUCCESS;
+}
+
+int sf_analyze(sf_t *sf) {
+  if (!sf) return SF_ERR_NULL;
+  if (sf->info.analyzed) return SF_SUCCESS;
+  return analyze(sf->g, sf->hp, sf->info);
+}
+
+int sf_setup(sf_t *sf, sf_stream_t stream) {
+  if (!sf) return SF_ERR_NULL;
+  if (sf->setup) return SF_SUCCESS;
+  int rc = sf_analyze(sf);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&sf->device) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  HostPlan &h = sf->hp;
+  // move tiles: slices of 4096 units of each remote segment
+  sf->h_move_tiles.clear();
+  for (size_t i = 0; i < h.segs.size(); ++i)
+    for (int64_t k0 = 0; k0 < h.segs[i].n; k0 += 4096)
+      sf->h_move_tiles.push_back(Tile{T_RUN, int32_t(i), int32_t(k0), int32_t(std::min<int64_t>(4096, h.segs[i].n - k0))});
+  BlobBuilder b;
+  const size_t o_runs = b.add(h.runs), o_ridx = b.add(h.ts_ridx), o_lidx = b.add(h.ts_lidx),
+               o_tst = b.add(h.ts_tiles), o_tss = b.add(h.ts_self_tiles), o_tsr = b.add(h.ts_remote_tiles),
+               o_segs = b.add(h.segs), o_mv = b.add(sf->h_move_tiles), o_mr = b.add(h.mruns), o_mask = b.add(h.mask),
+               o_prr = b.add(h.pr_root), o_prl = b.add(h.pr_leaf), o_mro = b.add(h.m_root), o_mpt = b.add(h.m_ptr),
+               o_mle = b.add(h.m_leaf), o_msl = b.add(h.m_slot), o_mct = b.add(h.m_ctr), o_chm = b.add(h.ch_m),
+               o_che = b.add(h.ch_e0), o_rf = b.add(h.rm_fold_tiles), o_rw = b.add(h.rm_winner_tiles),
+               o_rfe = b.add(h.rm_fetch_tiles);
+  const size_t bytes = std::max<size_t>(b.host.size(), 256);
+  if (cudaMalloc(&sf->blob.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_ALLOC;
+  }
+  sf->blob.bytes = bytes;
+  if (!b.host.empty() && cudaMemcpyAsync(sf->blob.p, b.host.data(), b.host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SF_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SF_ERR_CUDA;
+  char *base = static_cast<char *>(sf->blob.p);
+  DevPlan &d = sf->dp;
+  d.runs = reinterpret_cast<const Run *>(base + o_runs);
+  d.ts_ridx = reinterpret_cast<const int32_t *>(base + o_ridx);
+  d.ts_lidx = reinterpret_cast<const int32_t *>(base + o_lidx);
+  d.ts_tiles = reinterpret_cast<const Tile *>(base + o_tst);
+  d.ts_self_tiles = reinterpret_cast<const Tile *>(base + o_tss);
+  d.ts_remote_tiles = reinterpret_cast<const Tile *>(base + o_tsr);
+  d.segs = reinterpret_cast<const SegCopy *>(base + o_segs);
+  d.n_ts_tiles = int32_t(h.ts_tiles.size());
+  d.n_ts_self_tiles = int32_t(h.ts_self_tiles.size());
+  d.n_ts_remote_tiles = int32_t(h.ts_remote_tiles.size());
+  d.n_segs = int32_t(h.segs.size());
+  d.remote_units = h.remote_units;
+  sf->move_tiles = reinterpret_cast<const Tile *>(base + o_mv);
+  sf->n_move_tiles = int32_t(sf->h_move_tiles.size());
+  d.mruns = reinterpret_cast<const MaskedRun *>(base + o_mr);
+  d.mask = reinterpret_cast<const uint32_t *>(base + o_mask);
+  d.pr_root = reinterpret_cast<const int32_t *>(base + o_prr);
+  d.pr_leaf = reinterpret_cast<const int32_t *>(base + o_prl);
+  d.m_root = reinterpret_cast<const int32_t *>(base + o_mro);
+  d.m_ptr = reinterpret_cast<const int32_t *>(base + o_mpt);
+  d.m_leaf = reinterpret_cast<const int32_t *>(base + o_mle);
+  d.m_slot = reinterpret_cast<const int32_t *>(base + o_msl);
+  d.m_ctr = reinterpret_cast<const int32_t *>(base + o_mct);
+  d.ch_m = reinterpret_cast<const int32_t *>(base + o_chm);
+  d.ch_e0 = reinterpret_cast<const int32_t *>(base + o_che);
+  d.rm_fold_tiles = reinterpret_cast<const Tile *>(base + o_rf);
+  d.rm_winner_tiles = reinterpret_cast<const Tile *>(base + o_rw);
+  d.rm_fetch_tiles = reinterpret_cast<const Tile *>(base + o_rfe);
+  d.n_rm_fold_tiles = int32_t(h.rm_fold_tiles.size());
+  d.n_rm_winner_tiles = int32_t(h.rm_winner_tiles.size());
+  d.n_rm_fetch_tiles = int32_t(h.rm_fetch_tiles.size());
+  d.n_multi = int32_t(h.m_root.size());
+  d.n_partial_slots = h.n_partial_slots;
+  d.n_counters = h.n_counters;
+  // fold scratch for units up to 16 bytes, so common operations allocate nothing later
+  if ((rc = ensure(sf->partial, size_t(h.n_partial_slots) * 16, false, s)) ||
+      (rc = ensure(sf->counter, size_t(h.n_counters) * 4 * 8, true, s)))
+    return rc;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SF_ERR_CUDA;
+  sf->info.device_plan_bytes = int64_t(bytes);
+  sf->info.setup_done = 1;
+  sf->setup = true;
+  return SF_SUCCESS;
+}
+
+int sf_get_layout(const sf_t *sf, int64_t *rootoff, int64_t *leafoff) {
+  if (!sf || !rootoff || !leafoff) return SF_ERR_NULL;
+  for (int32_t p = 0; p <= sf->g.P; ++p) {
+    rootoff[p] = sf->g.rootoff[p];
+    leafoff[p] = sf->g.leafoff[p];
+  }
+  return SF_SUCCESS;
+}
+
+int sf_get_info(const sf_t *sf, sf_info *info) {
+  if (!sf || !info) return SF_ERR_NULL;
+  *info = sf->info;
+  return SF_SUCCESS;
+}
+
+int sf_set_mode(sf_t *sf, int32_t mode) {
+  if (!sf) return SF_ERR_NULL;
+  if (mode < SF_MODE_AUTO || mode > SF_MODE_DETERMINISTIC) return SF_ERR_ARG;
+  sf->mode = mode;
+  return SF_SUCCESS;
+}
+
+int sf_set_path(sf_t *sf, int32_t path) {
+  if (!sf) return SF_ERR_NULL;
+  if (path < SF_PATH_AUTO || path > SF_PATH_ROOT_MAJOR) return SF_ERR_ARG;
+  sf->path = path;
+  return SF_SUCCESS;
+}
+
+int sf_bcast_begin(sf_t *sf, sf_unit unit, const void *rootdata, void *leafdata, int32_t op, sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  const int w = elem_size(unit.dtype);
+  if ((sf->info.nroots_total && (rc = check_ptr(rootdata, w))) ||
+      (sf->info.leaf_extent_total && (rc = check_ptr(leafdata, w))))
+    return rc;
+  if (find_pending(sf, K_BCAST, unit, rootdata, leafdata, nullptr, op, 0, 0)) return SF_ERR_PENDING;
+  int finish = 0;
+  if ((rc = bcast_launch(sf, unit, rootdata, leafdata, op, static_cast<cudaStream_t>(stream), bcast_path(sf), &finish)))
+    return rc;
+  sf->pending.push_back(Pending{K_BCAST, unit, rootdata, leafdata, nullptr, op, 0, 0, finish});
+  return SF_SUCCESS;
+}
+
+int sf_bcast_end(sf_t *sf, sf_unit unit, const void *rootdata, void *leafdata, int32_t op, sf_stream_t stream) {
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_BCAST, unit, rootdata, leafdata, nullptr, op, 0, 0);
+  if (!pd) return SF_ERR_NO_PENDING;
+  const int finish = pd->finish;
+  drop_pending(sf, pd);
+  if (finish) return bcast_finish(sf, unit, rootdata, leafdata, op, static_cast<cudaStream_t>(stream));
+  return SF_SUCCESS;
+}
+
+int sf_reduce_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op, sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  const int w = elem_size(unit.dtype);
+  if ((sf->info.nroots_total && (rc = check_ptr(rootdata, w))) ||
+      (sf->info.leaf_extent_total && (rc = check_ptr(leafdata, w))))
+    return rc;
+  if (find_pending(sf, K_REDUCE, unit, leafdata, rootdata, nullptr, op, 0, 0)) return SF_ERR_PENDING;
+  if ((rc = reduce_launch(sf, unit, leafdata, rootdata, op, static_cast<cudaStream_t>(stream)))) return rc;
+  sf->pending.push_back(Pending{K_REDUCE, unit, leafdata, rootdata, nullptr, op, 0, 0, 0});
+  return SF_SUCCESS;
+}
+
+int sf_reduce_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op, sf_stream_t stream) {
+  (void)stream;
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_REDUCE, unit, leafdata, rootdata, nullptr, op, 0, 0);
+  if (!pd) return SF_ERR_NO_PENDING;
+  drop_pending(sf, pd);
+  return SF_SUCCESS;
+}
+
+int sf_fetch_and_op_begin(sf_t *sf, sf_unit unit, void *rootdata, const void *leafdata, void *leafupdate, int32_t op,
+                          sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  const int w = elem_size(unit.dtype);
+  if (sf->info.nroots_total && (rc = check_ptr(rootdata, w))) return rc;
+  if (sf->info.leaf_extent_total && ((rc = check_ptr(leafdata, w)) || (rc = check_ptr(leafupdate, w)))) return rc;
+  if (sf->mode == SF_MODE_ATOMIC && unit.bs != 1) return SF_ERR_UNSUPPORTED;
+  if (find_pending(sf, K_FETCH, unit, rootdata, leafdata, leafupdate, op, 0, 0)) return SF_ERR_PENDING;
+  if ((rc = fetch_launch(sf, unit, rootdata, leafdata, leafupdate, op, static_cast<cudaStream_t>(stream)))) return rc;
+  sf->pending.push_back(Pending{K_FETCH, unit, rootdata, leafdata, leafupdate, op, 0, 0, 0});
+  return SF_SUCCESS;
+}
+
+int sf_fetch_and_op_end(sf_t *sf, sf_unit unit, void *rootdata, const void *leafdata, void *leafupdate, int32_t op,
+                        sf_stream_t stream) {
+  (void)stream;
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_FETCH, unit, rootdata, leafdata, leafupdate, op, 0, 0);
+  if (!pd) return SF_ERR_NO_PENDING;
+  drop_pending(sf, pd);
+  return SF_SUCCESS;
+}
+
+// ---- memtype variants: host buffers staged through library-owned device buffers ----------
+int sf_bcast_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t rootmtype, const void *rootdata, int32_t leafmtype,
+                                void *leafdata, int32_t op, sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  if ((rootmtype != SF_MEM_HOST && rootmtype != SF_MEM_DEVICE) || (leafmtype != SF_MEM_HOST && leafmtype != SF_MEM_DEVICE))
+    return SF_ERR_ARG;
+  if (find_pending(sf, K_BCAST_MT, unit, rootdata, leafdata, nullptr, op, rootmtype, leafmtype)) return SF_ERR_PENDING;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ub = size_t(elem_size(unit.dtype)) * unit.bs;
+  const size_t rb = size_t(sf->info.nroots_total) * ub, lb = size_t(sf->info.leaf_extent_total) * ub;
+  const void *droot = rootdata;
+  void *dleaf = leafdata;
+  if (rootmtype == SF_MEM_HOST) {
+    if ((rc = ensure(sf->stage_root, rb, false, s))) return rc;
+    if (rb && (rc = cuda_err(cudaMemcpyAsync(sf->stage_root.p, rootdata, rb, cudaMemcpyHostToDevice, s)))) return rc;
+    droot = sf->stage_root.p;
+  }
+  if (leafmtype == SF_MEM_HOST) {
+    if ((rc = ensure(sf->stage_leaf, lb, false, s))) return rc;
+    // every op reads the leaves it leaves untouched back out, so the whole leaf array goes in
+    if (lb && (rc = cuda_err(cudaMemcpyAsync(sf->stage_leaf.p, leafdata, lb, cudaMemcpyHostToDevice, s)))) return rc;
+    dleaf = sf->stage_leaf.p;
+  }
+  int finish = 0;
+  if ((rc = bcast_launch(sf, unit, droot, dleaf, op, s, bcast_path(sf), &finish))) return rc;
+  sf->pending.push_back(Pending{K_BCAST_MT, unit, rootdata, leafdata, nullptr, op, rootmtype, leafmtype, finish});
+  return SF_SUCCESS;
+}
+
+int sf_bcast_with_memtype_end(sf_t *sf, sf_unit unit, int32_t rootmtype, const void *rootdata, int32_t leafmtype,
+                              void *leafdata, int32_t op, sf_stream_t stream) {
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_BCAST_MT, unit, rootdata, leafdata, nullptr, op, rootmtype, leafmtype);
+  if (!pd) return SF_ERR_NO_PENDING;
+  const int finish = pd->finish;
+  drop_pending(sf, pd);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const void *droot = rootmtype == SF_MEM_HOST ? sf->stage_root.p : rootdata;
+  void *dleaf = leafmtype == SF_MEM_HOST ? sf->stage_leaf.p : leafdata;
+  int rc;
+  if (finish && (rc = bcast_finish(sf, unit, droot, dleaf, op, s))) return rc;
+  if (leafmtype == SF_MEM_HOST) {
+    const size_t lb = size_t(sf->info.leaf_extent_total) * elem_size(unit.dtype) * unit.bs;
+    if (lb && (rc = cuda_err(cudaMemcpyAsync(leafdata, sf->stage_leaf.p, lb, cudaMemcpyDeviceToHost, s)))) return rc;
+  }
+  return SF_SUCCESS;
+}
+
+int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata, int32_t rootmtype,
+                                 void *rootdata, int32_t op, sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  if ((rootmtype != SF_MEM_HOST && rootmtype != SF_MEM_DEVICE) || (leafmtype != SF_MEM_HOST && leafmtype != SF_MEM_DEVICE))
+    return SF_ERR_ARG;
+  if (find_pending(sf, K_REDUCE_MT, unit, leafdata, rootdata, nullptr, op, leafmtype, rootmtype)) return SF_ERR_PENDING;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ub = size_t(elem_size(unit.dtype)) * unit.bs;
+  const size_t rb = size_t(sf->info.nroots_total) * ub, lb = size_t(sf->info.leaf_extent_total) * ub;
+  const void *dleaf = leafdata;
+  void *droot = rootdata;
+  if (leafmtype == SF_MEM_HOST) {
+    if ((rc = ensure(sf->stage_leaf, lb, false, s))) return rc;
+    if (lb && (rc = cuda_err(cudaMemcpyAsync(sf->stage_leaf.p, leafdata, lb, cudaMemcpyHostToDevice, s)))) return rc;
+    dleaf = sf->stage_leaf.p;
+  }
+  if (rootmtype == SF_MEM_HOST) {
+    if ((rc = ensure(sf->stage_root, rb, false, s))) return rc;
+    if (rb && (rc = cuda_err(cudaMemcpyAsync(sf->stage_root.p, rootdata, rb, cudaMemcpyHostToDevice, s)))) return rc;
+    droot = sf->stage_root.p;
+  }
+  if ((rc = reduce_launch(sf, unit, dleaf, droot, op, s))) return rc;
+  sf->pending.push_back(Pending{K_REDUCE_MT, unit, leafdata, rootdata, nullptr, op, leafmtype, rootmtype, 0});
+  return SF_SUCCESS;
+}
+
+int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata, int32_t rootmtype,
+                               void *rootdata, int32_t op, sf_stream_t stream) {
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_REDUCE_MT, unit, leafdata, rootdata, nullptr, op, leafmtype, rootmtype);
+  if (!pd) return SF_ERR_NO_PENDING;
+  drop_pending(sf, pd);
+  if (rootmtype == SF_MEM_HOST) {
+    const size_t rb = size_t(sf->info.nroots_total) * elem_size(unit.dtype) * unit.bs;
+    if (rb) return cuda_err(cudaMemcpyAsync(rootdata, sf->stage_root.p, rb, cudaMemcpyDeviceToHost,
+                                            static_cast<cudaStream_t>(stream)));
+  }
+  return SF_SUCCESS;
+}
+
+int sf_destroy(sf_t *sf) {
+  if (!sf) return SF_SUCCESS;
+  if (!sf->pending.empty()) return SF_ERR_PENDING;
+  if (sf->setup) {
+    release(sf->blob);
+    release(sf->partial);
+    release(sf->counter);
+    release(sf->rootbuf);
+    release(sf->leafbuf);
+    release(sf->stage_root);
+    release(sf->stage_leaf);
+  }
+  delete sf;
+  return SF_SUCCESS;
+}
+
+const char *sf_error_string(int code) {
+  switch (code) {
+    case SF_SUCCESS: return "success";
+    case SF_ERR_ARG: return "invalid argument";
+    case SF_ERR_NULL: return "required pointer is NULL";
+    case SF_ERR_RANGE: return "root address or leaf index out of range";
+    case SF_ERR_DUP_LEAF: return "a rank lists the same leaf twice";
+    case SF_ERR_STATE: return "call out of order (sf_setup not done)";
+    case SF_ERR_NO_PENDING: return "End without a matching Begin";
+    case SF_ERR_PENDING: return "a Begin with these arguments is still pending";
+    case SF_ERR_UNSUPPORTED: return "combination not supported";
+    case SF_ERR_ALLOC: return "allocation failed";
+    case SF_ERR_CUDA: return "CUDA runtime error";
+    case SF_ERR_ALIGN: return "data pointer not aligned to the element size";
+    case SF_ERR_TOO_LARGE: return "sizes beyond 2^31-1 units";
+  }
+  return "unknown error code";
+}
+
+int64_t sf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// sf_launch.h -- host-side launchers of the kernels (runtime dtype/op/width -> template).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sf_kernels.cuh"
+
+namespace sfgb {
+
+// dtype codes are the SF_* codes of sf.h
+// Two-sided kernel: REPLACE copies (any dtype, vector width vb in {2,4,8,16}), plain ops for
+// Bcast (l2r = false), atomics for Reduce / FetchAndOp (l2r = true, vb = element size).
+cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsArgs &a,
+                      int ntiles, cudaStream_t s);
+cudaError_t launch_move(int vb, const MoveArgs &a, int ntiles, cudaStream_t s);
+cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
+
+// per-dtype instantiations (one translation unit each)
+template <typename T> cudaError_t launch_rm_t(int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsArgs &a, int ntiles, cudaStream_t s);
+
+// accumulator pack bytes of the fold for (dtype, op, vb): scratch sizing
+int acc_pack_bytes(int dtype, int op, int vb);
+
+}  // namespace sfgb

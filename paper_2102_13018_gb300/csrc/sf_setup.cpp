@@ -1,0 +1,461 @@
+// sf_setup.cpp -- the setup pass (PetscSFSetUp, Sec. III.A and V.A-B), host only.
+//
+// 1. Two-sided information (Sec. V.A): edges grouped by root rank p; inside p by leaf rank q
+//    with q == p first ("self moved to the head", Sec. V.B); canonical order inside a group.
+//    Root-rank-major order keeps the gathers of one root rank close in time (L2 reuse).
+// 2. Pattern detection (Sec. V.B): each (p, q) group is cut into runs.  A run whose root and
+//    leaf units both follow a multi-strided sub-block start + X*Y*k + X*j + i (contiguous runs
+//    are the 1-D case) carries six numbers instead of two index arrays; a run with one side
+//    contiguous keeps only the other side's indices.
+// 3. Duplicate detection (Sec. V.C): in-degree of every root; runs touching a root of
+//    in-degree > 1 are flagged for atomics.
+// 4. Root-major plan: single-leaf roots as masked contiguous runs (or explicit pairs),
+//    multi-leaf roots in CSR form with their leaves in canonical order, cut into blocks of
+//    FOLD_BLOCK leaves for the deterministic fold.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "sf_host.h"
+
+namespace sfgb {
+
+namespace {
+constexpr int64_t kMaxUnits = (int64_t(1) << 31) - 1;
+constexpr int64_t kMinPatternEdges = 64;   // smallest run worth a pattern descriptor
+constexpr int64_t kMinMaskedSingles = 64;  // smallest masked run in the root-major plan
+constexpr int64_t kMaxMaskGap = 32;        // longest stretch of skipped roots inside one
+}  // namespace
+
+int build_graph(int32_t P, const int64_t nroots[], const int64_t nleaves[],
+                const int64_t *const ilocal[], const sf_node *const iremote[], Graph &g) {
+  if (P < 1) return SF_ERR_ARG;
+  if (!nroots || !nleaves) return SF_ERR_NULL;
+  g = Graph();
+  g.P = P;
+  try {
+    g.nroots.assign(nroots, nroots + P);
+    g.nleaves.assign(nleaves, nleaves + P);
+    g.rootoff.assign(P + 1, 0);
+    g.leafoff.assign(P + 1, 0);
+    g.edgeoff.assign(P + 1, 0);
+    for (int32_t p = 0; p < P; ++p) {
+      if (nroots[p] < 0 || nleaves[p] < 0) return SF_ERR_ARG;
+      g.rootoff[p + 1] = g.rootoff[p] + nroots[p];
+      g.edgeoff[p + 1] = g.edgeoff[p] + nleaves[p];
+      if (g.rootoff[p + 1] > kMaxUnits || g.edgeoff[p + 1] > kMaxUnits) return SF_ERR_TOO_LARGE;
+    }
+    g.E = g.edgeoff[P];
+    g.has_ilocal.assign(P, 0);
+    g.ilocal.assign(g.E, 0);
+    g.rrank.assign(g.E, 0);
+    g.rindex.assign(g.E, 0);
+    std::vector<uint64_t> seen;
+    for (int32_t q = 0; q < P; ++q) {
+      const int64_t n = nleaves[q], e0 = g.edgeoff[q];
+      if (n > 0 && (!iremote || !iremote[q])) return SF_ERR_NULL;
+      for (int64_t i = 0; i < n; ++i) {
+        const sf_node nd = iremote[q][i];
+        if (nd.rank < 0 || nd.rank >= P) return SF_ERR_RANGE;
+        if (nd.index < 0 || nd.index >= nroots[nd.rank]) return SF_ERR_RANGE;
+        g.rrank[e0 + i] = nd.rank;
+        g.rindex[e0 + i] = nd.index;
+      }
+      int64_t extent = n;
+      if (ilocal && ilocal[q] && n > 0) {
+        int64_t mx = -1;
+        for (int64_t i = 0; i < n; ++i) {
+          const int64_t l = ilocal[q][i];
+          if (l < 0) return SF_ERR_RANGE;
+          mx = std::max(mx, l);
+        }
+        extent = mx + 1;
+        if (extent > kMaxUnits) return SF_ERR_TOO_LARGE;
+        seen.assign((extent + 63) / 64, 0);
+        for (int64_t i = 0; i < n; ++i) {
+          const int64_t l = ilocal[q][i];
+          uint64_t &w = seen[l >> 6];
+          const uint64_t bit = uint64_t(1) << (l & 63);
+          if (w & bit) return SF_ERR_DUP_LEAF;
+          w |= bit;
+          g.ilocal[e0 + i] = l;
+        }
+        g.has_ilocal[q] = 1;
+      }
+      g.leafoff[q + 1] = g.leafoff[q] + extent;
+      if (g.leafoff[q + 1] > kMaxUnits) return SF_ERR_TOO_LARGE;
+    }
+  } catch (const std::bad_alloc &) {
+    return SF_ERR_ALLOC;
+  }
+  return SF_SUCCESS;
+}
+
+namespace {
+
+struct RunBuilder {
+  HostPlan &plan;
+  const int64_t *A;   // root units of the group, in group order
+  const int64_t *B;   // leaf units
+  int64_t n;
+  int32_t base_flags;
+  std::vector<int64_t> pending;   // positions of edges waiting for a both-indexed run
+
+  void emit(int64_t k, int32_t cnt, int32_t nx, int32_t ny, int64_t rsy, int64_t rsz,
+            int64_t lsy, int64_t lsz, int32_t idx_flags) {
+    Run r{};
+    r.root0 = A[k];
+    r.leaf0 = B[k];
+    r.rsy = rsy;
+    r.rsz = rsz;
+    r.lsy = lsy;
+    r.lsz = lsz;
+    r.n = cnt;
+    r.nx = nx;
+    r.ny = ny;
+    r.flags = base_flags | idx_flags;
+    r.idx0 = int64_t(plan.ts_ridx.size());
+    if (idx_flags) {
+      for (int64_t t = 0; t < cnt; ++t) {
+        plan.ts_ridx.push_back(int32_t(A[k + t]));
+        plan.ts_lidx.push_back(int32_t(B[k + t]));
+      }
+    }
+    plan.runs.push_back(r);
+  }
+
+  void flush_pending() {
+    if (pending.empty()) return;
+    // pending positions are consecutive in the group
+    const int64_t k = pending.front();
+    emit(k, int32_t(pending.size()), int32_t(pending.size()), 1, 0, 0, 0, 0,
+         RUN_ROOT_IDX | RUN_LEAF_IDX);
+    pending.clear();
+  }
+
+  bool rows_match(int64_t r0, int64_t nx, int64_t a0, int64_t b0) const {
+    for (int64_t t = 0; t < nx; ++t)
+      if (A[r0 + t] != a0 + t || B[r0 + t] != b0 + t) return false;
+    return true;
+  }
+
+  void run() {
+    int64_t k = 0;
+    while (k < n) {
+      // joint multi-strided sub-block, both sides
+      int64_t nx = 1;
+      while (k + nx < n && A[k + nx] == A[k + nx - 1] + 1 && B[k + nx] == B[k + nx - 1] + 1) ++nx;
+      int64_t ny = 1, nz = 1, rsy = 0, lsy = 0, rsz = 0, lsz = 0;
+      if (k + 2 * nx <= n) {
+        rsy = A[k + nx] - A[k];
+        lsy = B[k + nx] - B[k];
+        while (k + (ny + 1) * nx <= n && rows_match(k + ny * nx, nx, A[k] + ny * rsy, B[k] + ny * lsy)) ++ny;
+        if (ny == 1) rsy = lsy = 0;
+        const int64_t plane = nx * ny;
+        if (k + 2 * plane <= n) {
+          rsz = A[k + plane] - A[k];
+          lsz = B[k + plane] - B[k];
+          auto plane_ok = [&](int64_t z) {
+            for (int64_t j = 0; j < ny; ++j)
+              if (!rows_match(k + z * plane + j * nx, nx, A[k] + z * rsz + j * rsy, B[k] + z * lsz + j * lsy))
+                return false;
+            return true;
+          };
+          while (k + (nz + 1) * plane <= n && plane_ok(nz)) ++nz;
+          if (nz == 1) rsz = lsz = 0;
+        }
+      }
+      const int64_t total = nx * ny * nz;
+      if (total >= kMinPatternEdges) {
+        flush_pending();
+        emit(k, int32_t(total), int32_t(nx), int32_t(ny), rsy, rsz, lsy, lsz, 0);
+        k += total;
+        continue;
+      }
+      // one side contiguous, the other indexed
+      int64_t lb = 1, la = 1;
+      while (k + lb < n && B[k + lb] == B[k + lb - 1] + 1) ++lb;
+      while (k + la < n && A[k + la] == A[k + la - 1] + 1) ++la;
+      if (lb >= kMinPatternEdges && lb >= la) {
+        flush_pending();
+        emit(k, int32_t(lb), int32_t(lb), 1, 0, 0, 0, 0, RUN_ROOT_IDX);
+        k += lb;
+        continue;
+      }
+      if (la >= kMinPatternEdges) {
+        flush_pending();
+        emit(k, int32_t(la), int32_t(la), 1, 0, 0, 0, 0, RUN_LEAF_IDX);
+        k += la;
+        continue;
+      }
+      pending.push_back(k);
+      ++k;
+    }
+    flush_pending();
+  }
+};
+
+void push_tiles(std::vector<Tile> &out, int32_t kind, int32_t a, int64_t n, int64_t per) {
+  for (int64_t k0 = 0; k0 < n; k0 += per)
+    out.push_back(Tile{kind, a, int32_t(k0), int32_t(std::min<int64_t>(per, n - k0))});
+}
+
+}  // namespace
+
+int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
+  try {
+    plan = HostPlan();
+    const int32_t P = g.P;
+    const int64_t E = g.E, NR = g.rootoff[P];
+    std::vector<int64_t> leafu(E), rootu(E);
+    std::vector<int32_t> lq(E);
+    for (int32_t q = 0; q < P; ++q)
+      for (int64_t i = 0, e = g.edgeoff[q]; e < g.edgeoff[q + 1]; ++i, ++e) {
+        leafu[e] = g.leafoff[q] + (g.has_ilocal[q] ? g.ilocal[e] : i);
+        rootu[e] = g.rootoff[g.rrank[e]] + g.rindex[e];
+        lq[e] = q;
+      }
+    std::vector<int32_t> deg(NR, 0);
+    for (int64_t e = 0; e < E; ++e) deg[rootu[e]]++;
+
+    // ---- two-sided grouping: key = p*(P+1) + (q == p ? 0 : q + 1), stable counting sort
+    const int64_t nkeys = int64_t(P) * (P + 1);
+    std::vector<int64_t> cnt(nkeys + 1, 0), order(E);
+    auto key_of = [&](int64_t e) {
+      const int64_t p = g.rrank[e], q = lq[e];
+      return p * (P + 1) + (q == p ? 0 : q + 1);
+    };
+    for (int64_t e = 0; e < E; ++e) cnt[key_of(e) + 1]++;
+    for (int64_t k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
+    {
+      std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+      for (int64_t e = 0; e < E; ++e) order[fill[key_of(e)]++] = e;
+    }
+    // leaf-side buffer offsets: segments ordered (q, p) for the receive side
+    std::vector<int64_t> lbuf_off(nkeys, -1);
+    {
+      int64_t off = 0;
+      for (int32_t q = 0; q < P; ++q)
+        for (int32_t p = 0; p < P; ++p) {
+          if (p == q) continue;
+          const int64_t key = int64_t(p) * (P + 1) + (q + 1);
+          const int64_t n = cnt[key + 1] - cnt[key];
+          if (n) { lbuf_off[key] = off; off += n; }
+        }
+      plan.remote_units = off;
+    }
+    std::vector<int64_t> A, B;
+    int64_t rbuf = 0;
+    for (int64_t key = 0; key < nkeys; ++key) {
+      const int64_t s = cnt[key], t = cnt[key + 1];
+      if (s == t) continue;
+      info.segments++;
+      const bool self = (key % (P + 1)) == 0;
+      A.resize(t - s);
+      B.resize(t - s);
+      bool dup = false;
+      for (int64_t k = s; k < t; ++k) {
+        A[k - s] = rootu[order[k]];
+        B[k - s] = leafu[order[k]];
+        dup |= deg[A[k - s]] > 1;
+      }
+      const size_t run_first = plan.runs.size();
+      RunBuilder rb{plan, A.data(), B.data(), t - s, int32_t((self ? RUN_SELF : 0) | (dup ? RUN_DUP : 0)), {}};
+      rb.run();
+      if (self) {
+        info.self_edges += t - s;
+      } else {
+        // buffer offsets of each run inside this segment's chunks
+        int64_t pos = 0;
+        for (size_t r = run_first; r < plan.runs.size(); ++r) {
+          plan.runs[r].rbuf0 = rbuf + pos;
+          plan.runs[r].lbuf0 = lbuf_off[key] + pos;
+          pos += plan.runs[r].n;
+        }
+        plan.segs.push_back(SegCopy{rbuf, lbuf_off[key], t - s});
+        rbuf += t - s;
+      }
+    }
+    for (size_t r = 0; r < plan.runs.size(); ++r) {
+      const Run &run = plan.runs[r];
+      push_tiles(plan.ts_tiles, T_RUN, int32_t(r), run.n, TS_TILE_EDGES);
+      push_tiles((run.flags & RUN_SELF) ? plan.ts_self_tiles : plan.ts_remote_tiles, T_RUN, int32_t(r), run.n,
+                 TS_TILE_EDGES);
+      info.runs++;
+      const int32_t idx = run.flags & (RUN_ROOT_IDX | RUN_LEAF_IDX);
+      if (idx == 0) {
+        info.runs_pattern++;
+        if (run.ny > 1 || run.nx < run.n) info.runs_3d++;
+        info.edges_both_pattern += run.n;
+      } else if (idx == (RUN_ROOT_IDX | RUN_LEAF_IDX)) {
+        info.edges_two_indexed += run.n;
+      } else {
+        info.edges_one_indexed += run.n;
+      }
+    }
+
+    // ---- root-major plan
+    // multi roots: CSR of leaves in canonical order
+    std::vector<int32_t> mid(NR, -1);
+    int32_t M = 0;
+    int64_t multi_edges = 0;
+    for (int64_t r = 0; r < NR; ++r)
+      if (deg[r] >= 2) { mid[r] = M++; multi_edges += deg[r]; }
+    plan.m_root.resize(M);
+    plan.m_ptr.assign(M + 1, 0);
+    for (int64_t r = 0; r < NR; ++r)
+      if (mid[r] >= 0) { plan.m_root[mid[r]] = int32_t(r); plan.m_ptr[mid[r] + 1] = deg[r]; }
+    for (int32_t m = 0; m < M; ++m) plan.m_ptr[m + 1] += plan.m_ptr[m];
+    plan.m_leaf.resize(multi_edges);
+    {
+      std::vector<int32_t> fill(plan.m_ptr.begin(), plan.m_ptr.end() - 1);
+      for (int64_t e = 0; e < E; ++e) {
+        const int32_t m = mid[rootu[e]];
+        if (m >= 0) plan.m_leaf[fill[m]++] = int32_t(leafu[e]);
+      }
+    }
+    // single-leaf roots
+    std::vector<int64_t> sleaf(NR, -1);
+    for (int64_t e = 0; e < E; ++e)
+      if (deg[rootu[e]] == 1) sleaf[rootu[e]] = leafu[e];
+    {
+      int64_t r0 = -1, l0 = 0, last = -1;
+      std::vector<int64_t> members;
+      auto close = [&]() {
+        if (members.empty()) return;
+        if (int64_t(members.size()) >= kMinMaskedSingles) {
+          MaskedRun mr{};
+          mr.root0 = r0;
+          mr.leaf0 = l0;
+          mr.n = int32_t(last - r0 + 1);
+          mr.mask0 = int64_t(plan.mask.size()) * 32;
+          plan.mask.resize(plan.mask.size() + (mr.n + 31) / 32, 0u);
+          for (int64_t r : members) {
+            const int64_t bit = mr.mask0 + (r - r0);
+            plan.mask[bit >> 5] |= 1u << (bit & 31);
+          }
+          plan.mruns.push_back(mr);
+        } else {
+          for (int64_t r : members) {
+            plan.pr_root.push_back(int32_t(r));
+            plan.pr_leaf.push_back(int32_t(sleaf[r]));
+          }
+        }
+        members.clear();
+      };
+      for (int64_t r = 0; r < NR; ++r) {
+        if (deg[r] != 1) continue;
+        const bool extend = !members.empty() && r - last <= kMaxMaskGap && sleaf[r] - l0 == r - r0 &&
+                            r - r0 < (int64_t(1) << 30);
+        if (!extend) {
+          close();
+          r0 = r;
+          l0 = sleaf[r];
+        }
+        members.push_back(r);
+        last = r;
+      }
+      close();
+    }
+    // fold blocks of multi roots
+    plan.m_slot.assign(M, -1);
+    plan.m_ctr.assign(M, -1);
+    std::vector<uint8_t> heavy(M, 0);
+    for (int32_t m = 0; m < M; ++m) {
+      const int32_t d = plan.m_ptr[m + 1] - plan.m_ptr[m];
+      const int32_t nch = (d + FOLD_BLOCK - 1) / FOLD_BLOCK;
+      for (int32_t c = 0; c < nch; ++c) {
+        plan.ch_m.push_back(m);
+        plan.ch_e0.push_back(plan.m_ptr[m] + c * FOLD_BLOCK);
+      }
+      if (nch > 1) {
+        plan.m_slot[m] = plan.n_partial_slots;
+        plan.n_partial_slots += nch;
+        plan.m_ctr[m] = plan.n_counters++;
+      }
+      heavy[m] = nch >= 16;
+    }
+    // tiles, ordered by the first root they touch (heavy multi roots first)
+    struct Keyed { int64_t key; Tile t; };
+    std::vector<Keyed> common;
+    for (size_t i = 0; i < plan.mruns.size(); ++i)
+      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += RM_TILE_EDGES)
+        common.push_back({plan.mruns[i].root0 + k0,
+                          Tile{T_MASKED, int32_t(i), int32_t(k0),
+                               int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.mruns[i].n - k0))}});
+    for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += RM_TILE_EDGES)
+      common.push_back({plan.pr_root[i], Tile{T_PAIRS, int32_t(i), 0,
+                                              int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.pr_root.size() - i))}});
+    const int64_t heavy_key = -(int64_t(1) << 40);
+    auto finish = [&](std::vector<Keyed> extra, std::vector<Tile> &out) {
+      extra.insert(extra.end(), common.begin(), common.end());
+      std::stable_sort(extra.begin(), extra.end(), [](const Keyed &a, const Keyed &b) { return a.key < b.key; });
+      out.clear();
+      for (auto &k : extra) out.push_back(k.t);
+    };
+    {
+      std::vector<Keyed> ch;
+      const int64_t nchunks = int64_t(plan.ch_m.size());
+      int64_t c = 0;
+      while (c < nchunks) {
+        const int32_t m = plan.ch_m[c];
+        int64_t c1 = c;
+        if (heavy[m]) {   // a heavy root's blocks get tiles of their own
+          while (c1 < nchunks && plan.ch_m[c1] == m && c1 - c < RM_TILE_CHUNKS) ++c1;
+        } else {
+          while (c1 < nchunks && !heavy[plan.ch_m[c1]] && c1 - c < RM_TILE_CHUNKS) ++c1;
+        }
+        ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]),
+                      Tile{T_CHUNKS, int32_t(c), 0, int32_t(c1 - c)}});
+        c = c1;
+      }
+      finish(ch, plan.rm_fold_tiles);
+    }
+    {
+      std::vector<Keyed> w;
+      for (int32_t m = 0; m < M; m += RM_TILE_ROOTS)
+        w.push_back({plan.m_root[m], Tile{T_WINNERS, m, 0, std::min<int32_t>(RM_TILE_ROOTS, M - m)}});
+      finish(w, plan.rm_winner_tiles);
+    }
+    {
+      std::vector<Keyed> f;
+      int32_t m = 0;
+      while (m < M) {
+        int32_t m1 = m;
+        int64_t edges = 0;
+        while (m1 < M && m1 - m < RM_TILE_FETCH && (edges < 4096 || m1 == m)) {
+          edges += plan.m_ptr[m1 + 1] - plan.m_ptr[m1];
+          ++m1;
+        }
+        f.push_back({plan.m_root[m], Tile{T_FETCH, m, 0, m1 - m}});
+        m = m1;
+      }
+      finish(f, plan.rm_fetch_tiles);
+    }
+
+    // ---- statistics
+    info.nranks = P;
+    info.nroots_total = NR;
+    info.leaf_extent_total = g.leafoff[P];
+    info.nedges = E;
+    for (int64_t r = 0; r < NR; ++r) {
+      info.max_in_degree = std::max<int64_t>(info.max_in_degree, deg[r]);
+      info.connected_roots += deg[r] > 0;
+    }
+    info.has_dup_roots = info.max_in_degree > 1;
+    info.multi_roots = M;
+    info.multi_edges = multi_edges;
+    info.rm_masked_runs = int64_t(plan.mruns.size());
+    for (auto &mr : plan.mruns)
+      for (int32_t k = 0; k < mr.n; ++k)
+        info.rm_masked_edges += (plan.mask[(mr.mask0 + k) >> 5] >> ((mr.mask0 + k) & 31)) & 1u;
+    info.rm_pairs = int64_t(plan.pr_root.size());
+    info.rm_chunks = int64_t(plan.ch_m.size());
+    info.analyzed = 1;
+  } catch (const std::bad_alloc &) {
+    return SF_ERR_ALLOC;
+  }
+  return SF_SUCCESS;
+}
+
+}  // namespace sfgb

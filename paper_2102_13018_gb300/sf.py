@@ -1,0 +1,234 @@
+"""StarForest: Python handle over the C ABI (argument marshalling only).
+
+Every step of Bcast / Reduce / FetchAndOp runs in libsfgb's kernels; this module converts
+arrays to pointers, infers the unit from a tensor's dtype and shape, and passes the current
+torch CUDA stream.  PyTorch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _abi
+from ._abi import check, sf_info, sf_node, sf_unit
+
+OPS = {"REPLACE": _abi.SF_REPLACE, "SUM": _abi.SF_SUM, "MIN": _abi.SF_MIN, "MAX": _abi.SF_MAX}
+MODES = {"auto": _abi.SF_MODE_AUTO, "atomic": _abi.SF_MODE_ATOMIC, "deterministic": _abi.SF_MODE_DETERMINISTIC}
+PATHS = {"auto": _abi.SF_PATH_AUTO, "fused": _abi.SF_PATH_FUSED, "three_phase": _abi.SF_PATH_THREE_PHASE,
+         "root_major": _abi.SF_PATH_ROOT_MAJOR}
+DTYPE_NAMES = {"int32": _abi.SF_INT32, "int64": _abi.SF_INT64, "fp32": _abi.SF_FP32, "fp64": _abi.SF_FP64,
+               "bf16": _abi.SF_BF16}
+
+
+def _torch_dtype_code(t) -> int:
+    import torch
+    m = {torch.int32: _abi.SF_INT32, torch.int64: _abi.SF_INT64, torch.float32: _abi.SF_FP32,
+         torch.float64: _abi.SF_FP64, torch.bfloat16: _abi.SF_BF16}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _numpy_dtype_code(a: np.ndarray, bf16: bool = False) -> int:
+    if bf16:
+        assert a.dtype == np.uint16
+        return _abi.SF_BF16
+    m = {np.dtype(np.int32): _abi.SF_INT32, np.dtype(np.int64): _abi.SF_INT64,
+         np.dtype(np.float32): _abi.SF_FP32, np.dtype(np.float64): _abi.SF_FP64}
+    return m[a.dtype]
+
+
+class StarForest:
+    """A star forest over `nranks` simulated ranks (Sec. III.A).
+
+    nroots[p], nleaves[p]: sizes per rank; ilocal[p]: int array or None (contiguous leaves);
+    iremote_rank[p], iremote_index[p]: root address of each leaf.
+    """
+
+    def __init__(self, nroots: Sequence[int], nleaves: Sequence[int], ilocal, iremote_rank, iremote_index):
+        self._lib = _abi.load()
+        P = len(nroots)
+        self.nranks = P
+        self._nroots = np.ascontiguousarray(nroots, dtype=np.int64)
+        self._nleaves = np.ascontiguousarray(nleaves, dtype=np.int64)
+        if len(self._nleaves) != P:
+            raise ValueError("nroots and nleaves differ in length")
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        nodep = ctypes.POINTER(sf_node)
+        self._keep = []
+        il_arr = (i64p * P)()
+        ir_arr = (nodep * P)()
+        node_dt = np.dtype([("rank", "<i4"), ("index", "<i8")], align=True)
+        assert node_dt.itemsize == ctypes.sizeof(sf_node)
+        for p in range(P):
+            if ilocal is not None and ilocal[p] is not None:
+                a = np.ascontiguousarray(ilocal[p], dtype=np.int64)
+                self._keep.append(a)
+                il_arr[p] = a.ctypes.data_as(i64p)
+            n = int(self._nleaves[p])
+            nodes = np.zeros(max(n, 1), dtype=node_dt)
+            if n:
+                nodes["rank"][:n] = np.asarray(iremote_rank[p], dtype=np.int32)[:n]
+                nodes["index"][:n] = np.asarray(iremote_index[p], dtype=np.int64)[:n]
+            self._keep.append(nodes)
+            ir_arr[p] = ctypes.cast(nodes.ctypes.data, nodep)
+        h = ctypes.c_void_p()
+        check(self._lib.sf_create(P, self._nroots.ctypes.data_as(i64p), self._nleaves.ctypes.data_as(i64p),
+                                  il_arr, ir_arr, ctypes.byref(h)), "sf_create")
+        self._h = h
+        self._keep = None   # sf_create copied everything
+        ro = np.zeros(P + 1, np.int64)
+        lo = np.zeros(P + 1, np.int64)
+        check(self._lib.sf_get_layout(self._h, ro.ctypes.data_as(i64p), lo.ctypes.data_as(i64p)), "sf_get_layout")
+        self.rootoff, self.leafoff = ro, lo
+        self.nroots_total = int(ro[-1])
+        self.leaf_extent = int(lo[-1])
+
+    @classmethod
+    def from_forest(cls, f) -> "StarForest":
+        """From any object with nroots, nleaves, ilocal, iremote_rank, iremote_index."""
+        return cls(f.nroots, f.nleaves, f.ilocal, f.iremote_rank, f.iremote_index)
+
+    # ---------------------------------------------------------------- lifecycle
+    def analyze(self) -> "StarForest":
+        check(self._lib.sf_analyze(self._h), "sf_analyze")
+        return self
+
+    def setup(self, stream=None) -> "StarForest":
+        check(self._lib.sf_setup(self._h, self._stream(stream)), "sf_setup")
+        return self
+
+    def info(self) -> dict:
+        inf = sf_info()
+        check(self._lib.sf_get_info(self._h, ctypes.byref(inf)), "sf_get_info")
+        return inf.as_dict()
+
+    def set_mode(self, mode: str) -> "StarForest":
+        check(self._lib.sf_set_mode(self._h, MODES[mode]), "sf_set_mode")
+        return self
+
+    def set_path(self, path: str) -> "StarForest":
+        check(self._lib.sf_set_path(self._h, PATHS[path]), "sf_set_path")
+        return self
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            check(self._lib.sf_destroy(self._h), "sf_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._lib.sf_destroy(self._h)
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- helpers
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available() and torch.cuda.is_initialized():
+                    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            except Exception:
+                pass
+            return ctypes.c_void_p(0)
+        if isinstance(stream, int):
+            return ctypes.c_void_p(stream)
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    def _unit(self, t, units: int, bs: Optional[int]) -> sf_unit:
+        code = _torch_dtype_code(t)
+        if bs is None:
+            if units == 0:
+                bs = t.shape[-1] if t.dim() > 1 else 1
+            else:
+                if t.numel() % units:
+                    raise ValueError(f"tensor of {t.numel()} elements is not {units} units")
+                bs = t.numel() // units
+        return sf_unit(code, int(bs))
+
+    @staticmethod
+    def _ptr(t):
+        if t is None:
+            return None
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ---------------------------------------------------------------- operations (device tensors)
+    def bcast_begin(self, rootdata, leafdata, op: str = "REPLACE", bs: Optional[int] = None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_bcast_begin(self._h, u, self._ptr(rootdata), self._ptr(leafdata), OPS[op],
+                                       self._stream(stream)), "sf_bcast_begin")
+
+    def bcast_end(self, rootdata, leafdata, op: str = "REPLACE", bs: Optional[int] = None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_bcast_end(self._h, u, self._ptr(rootdata), self._ptr(leafdata), OPS[op],
+                                     self._stream(stream)), "sf_bcast_end")
+
+    def bcast(self, rootdata, leafdata, op: str = "REPLACE", bs: Optional[int] = None, stream=None):
+        self.bcast_begin(rootdata, leafdata, op, bs, stream)
+        self.bcast_end(rootdata, leafdata, op, bs, stream)
+        return leafdata
+
+    def reduce_begin(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_reduce_begin(self._h, u, self._ptr(leafdata), self._ptr(rootdata), OPS[op],
+                                        self._stream(stream)), "sf_reduce_begin")
+
+    def reduce_end(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_reduce_end(self._h, u, self._ptr(leafdata), self._ptr(rootdata), OPS[op],
+                                      self._stream(stream)), "sf_reduce_end")
+
+    def reduce(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
+        self.reduce_begin(leafdata, rootdata, op, bs, stream)
+        self.reduce_end(leafdata, rootdata, op, bs, stream)
+        return rootdata
+
+    def fetch_and_op_begin(self, rootdata, leafdata, leafupdate, op: str = "SUM", bs=None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_fetch_and_op_begin(self._h, u, self._ptr(rootdata), self._ptr(leafdata),
+                                              self._ptr(leafupdate), OPS[op], self._stream(stream)),
+              "sf_fetch_and_op_begin")
+
+    def fetch_and_op_end(self, rootdata, leafdata, leafupdate, op: str = "SUM", bs=None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_fetch_and_op_end(self._h, u, self._ptr(rootdata), self._ptr(leafdata),
+                                            self._ptr(leafupdate), OPS[op], self._stream(stream)),
+              "sf_fetch_and_op_end")
+
+    def fetch_and_op(self, rootdata, leafdata, leafupdate, op: str = "SUM", bs=None, stream=None):
+        self.fetch_and_op_begin(rootdata, leafdata, leafupdate, op, bs, stream)
+        self.fetch_and_op_end(rootdata, leafdata, leafupdate, op, bs, stream)
+        return leafupdate
+
+    # ---------------------------------------------------------------- host-buffer variants
+    def _mt(self, t):
+        return _abi.SF_MEM_DEVICE if t.is_cuda else _abi.SF_MEM_HOST
+
+    def bcast_memtype(self, rootdata, leafdata, op: str = "REPLACE", bs=None, stream=None):
+        """Bcast where either buffer may be a CPU tensor (pinned for asynchronous copies)."""
+        u = self._unit(rootdata, self.nroots_total, bs)
+        args = (self._h, u, self._mt(rootdata), self._ptr(rootdata), self._mt(leafdata), self._ptr(leafdata),
+                OPS[op], self._stream(stream))
+        check(self._lib.sf_bcast_with_memtype_begin(*args), "sf_bcast_with_memtype_begin")
+        check(self._lib.sf_bcast_with_memtype_end(*args), "sf_bcast_with_memtype_end")
+        return leafdata
+
+    def reduce_memtype(self, leafdata, rootdata, op: str = "SUM", bs=None, stream=None):
+        u = self._unit(rootdata, self.nroots_total, bs)
+        args = (self._h, u, self._mt(leafdata), self._ptr(leafdata), self._mt(rootdata), self._ptr(rootdata),
+                OPS[op], self._stream(stream))
+        check(self._lib.sf_reduce_with_memtype_begin(*args), "sf_reduce_with_memtype_begin")
+        check(self._lib.sf_reduce_with_memtype_end(*args), "sf_reduce_with_memtype_end")
+        return rootdata
+
+
+def launch_count() -> int:
+    """Kernels libsfgb has launched in this process."""
+    return int(_abi.load().sf_launch_count())

@@ -1,0 +1,160 @@
+"""C ABI surface and the host setup pass, on the CPU (no CUDA call needs a device here)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import sfgen
+from paper_2102_13018_gb300 import _abi, StarForest, SFError
+from tests import npref
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _abi.load()
+    names = _abi.declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_error_strings_cover_every_code():
+    lib = _abi.load()
+    for code in _abi.ERRORS:
+        s = lib.sf_error_string(code).decode()
+        assert s and s != "unknown error code"
+    assert lib.sf_error_string(999).decode() == "unknown error code"
+
+
+def _create_raw(P, nroots, nleaves, ilocal, rr, ri):
+    try:
+        StarForest(nroots, nleaves, ilocal, rr, ri)
+        return 0
+    except SFError as e:
+        return e.code
+
+
+@pytest.mark.parametrize("case,code", [
+    ("zero_ranks", "SF_ERR_ARG"),
+    ("negative_nroots", "SF_ERR_ARG"),
+    ("rank_out_of_range", "SF_ERR_RANGE"),
+    ("index_out_of_range", "SF_ERR_RANGE"),
+    ("negative_index", "SF_ERR_RANGE"),
+    ("negative_ilocal", "SF_ERR_RANGE"),
+    ("duplicate_ilocal", "SF_ERR_DUP_LEAF"),
+    ("ok", "SF_SUCCESS"),
+])
+def test_create_validation(case, code):
+    args = {
+        "zero_ranks": ([], [], None, [], []),
+        "negative_nroots": ([-1], [0], None, [[]], [[]]),
+        "rank_out_of_range": ([2, 2], [1, 0], None, [[2], []], [[0], []]),
+        "index_out_of_range": ([2, 2], [1, 0], None, [[1], []], [[2], []]),
+        "negative_index": ([2], [1], None, [[0]], [[-1]]),
+        "negative_ilocal": ([2], [1], [[-3]], [[0]], [[0]]),
+        "duplicate_ilocal": ([2], [2], [[5, 5]], [[0, 0]], [[0, 1]]),
+        "ok": ([2], [2], [[5, 1]], [[0, 0]], [[0, 1]]),
+    }[case]
+    assert _create_raw(len(args[0]), *args) == _abi.CODES[code]
+
+
+def test_create_null_pointers():
+    lib = _abi.load()
+    h = ctypes.c_void_p()
+    assert lib.sf_create(1, None, None, None, None, ctypes.byref(h)) == _abi.CODES["SF_ERR_NULL"]
+    n = (ctypes.c_int64 * 1)(1)
+    # nleaves > 0 but no iremote
+    assert lib.sf_create(1, n, n, None, None, ctypes.byref(h)) == _abi.CODES["SF_ERR_NULL"]
+    assert lib.sf_create(1, n, n, None, None, None) == _abi.CODES["SF_ERR_NULL"]
+
+
+def test_too_large_leaf_space_is_rejected():
+    code = _create_raw(1, [1], [1], [[1 << 40]], [[0]], [[0]])
+    assert code == _abi.CODES["SF_ERR_TOO_LARGE"]
+
+
+FORESTS = [sfgen.fig2(), sfgen.cfg1_plain_tiny()] + [sfgen.random_forest(s, P, 30, 40) for s, P in
+                                                       [(31, 1), (32, 4), (33, 9)]]
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_layout_matches_oracle(f):
+    sf = StarForest.from_forest(f)
+    ro, lo = oracle.layout(f)
+    assert np.array_equal(sf.rootoff, ro) and np.array_equal(sf.leafoff, lo)
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_analysis_statistics(f):
+    info = StarForest.from_forest(f).analyze().info()
+    L, R = npref.edge_arrays(f)
+    deg = np.bincount(R, minlength=info["nroots_total"])
+    assert info["nedges"] == len(L)
+    assert info["max_in_degree"] == (deg.max() if len(deg) else 0)
+    assert info["connected_roots"] == int((deg > 0).sum())
+    assert info["multi_roots"] == int((deg > 1).sum())
+    assert info["multi_edges"] == int(deg[deg > 1].sum())
+    assert info["has_dup_roots"] == int(deg.max() > 1)
+    # every edge lands in exactly one run class and one root-major class
+    assert info["edges_both_pattern"] + info["edges_one_indexed"] + info["edges_two_indexed"] == len(L)
+    assert info["rm_masked_edges"] + info["rm_pairs"] + info["multi_edges"] == len(L)
+    rank_of_leaf = np.concatenate([np.full(int(f.nleaves[q]), q) for q in range(f.nranks)]) if len(L) else []
+    rr = np.concatenate(f.iremote_rank) if len(L) else []
+    assert info["self_edges"] == int(np.sum(np.asarray(rank_of_leaf) == np.asarray(rr)))
+    pairs = {(int(a), int(b)) for a, b in zip(rr, rank_of_leaf)}
+    assert info["segments"] == len(pairs)
+    assert info["analyzed"] == 1 and info["setup_done"] == 0
+
+
+def test_fig2_analysis_by_hand():
+    info = StarForest.from_forest(sfgen.fig2()).analyze().info()
+    assert info["nroots_total"] == 9 and info["leaf_extent_total"] == 11
+    assert info["max_in_degree"] == 3 and info["multi_roots"] == 2 and info["multi_edges"] == 5
+    # (root rank, leaf rank) pairs: (1,0) (0,0) (2,1) (0,1) (0,2) (1,2)
+    assert info["segments"] == 6 and info["self_edges"] == 1
+
+
+def test_halo_is_index_free():
+    """3-D halo (Sec. V.B multi-strided sub-blocks): faces and edges become pattern runs;
+    only the 1-point corner groups keep indices."""
+    f = sfgen.cfg2_halo(128, 2)          # 64^3 owned points per rank, as at full size
+    info = StarForest.from_forest(f).analyze().info()
+    assert info["runs_3d"] > 0
+    corners = info["edges_two_indexed"] + info["edges_one_indexed"]
+    assert corners <= f.nranks             # one corner point per rank
+    assert info["edges_both_pattern"] >= 0.97 * info["nedges"]
+
+
+def test_spmv_scatter_patterns():
+    """Owned entries are one contiguous run per rank; ghost columns are contiguous on the
+    leaf side and need root indices only."""
+    f = sfgen.cfg3_spmv(1 << 15, 4)
+    info = StarForest.from_forest(f).analyze().info()
+    P = f.nranks
+    assert info["self_edges"] == f.nroots.sum()
+    assert info["edges_both_pattern"] >= f.nroots.sum()
+    assert info["edges_two_indexed"] <= 0.05 * info["nedges"]
+    assert info["rm_masked_runs"] >= P
+
+
+def test_operations_before_setup_fail_cleanly():
+    lib = _abi.load()
+    sf = StarForest.from_forest(sfgen.fig2())
+    u = _abi.sf_unit(_abi.SF_FP64, 1)
+    buf = ctypes.c_void_p(64)
+    assert lib.sf_bcast_begin(sf._h, u, buf, buf, 0, None) == _abi.CODES["SF_ERR_STATE"]
+    assert lib.sf_reduce_begin(sf._h, u, buf, buf, 1, None) == _abi.CODES["SF_ERR_STATE"]
+    assert lib.sf_bcast_end(sf._h, u, buf, buf, 0, None) == _abi.CODES["SF_ERR_NO_PENDING"]
+    assert lib.sf_set_mode(sf._h, 7) == _abi.CODES["SF_ERR_ARG"]
+    assert lib.sf_set_path(sf._h, -1) == _abi.CODES["SF_ERR_ARG"]
+    assert lib.sf_destroy(None) == 0
+
+
+def test_setup_without_a_device_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    sf = StarForest.from_forest(sfgen.fig2())
+    with pytest.raises(SFError) as ei:
+        sf.setup(stream=0)
+    assert ei.value.name == "SF_ERR_CUDA"

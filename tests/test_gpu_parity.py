@@ -1,0 +1,206 @@
+"""CUDA path vs oracle, element by element, through the C ABI (GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+import sfgen
+from tests.gpu_util import assert_atomic_sum_close, assert_bits_equal, make_data, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2102_13018_gb300 import StarForest, SFError, launch_count  # noqa: E402
+
+
+def small_forests():
+    fs = [sfgen.fig2(), sfgen.cfg1_plain_tiny(), sfgen.cfg2_halo(64, 4), sfgen.cfg3_spmv(1 << 15, 4),
+          sfgen.zipf_forest(77, 1, 20000, 3000, 4)]
+    fs += [sfgen.random_forest(s, P, 300, 400) for s, P in [(41, 1), (42, 3), (43, 8)]]
+    fs.append(sfgen.Forest(2, np.array([5, 0]), np.array([0, 0]), [None, None],
+                           [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int64)] * 2, name="empty"))
+    return fs
+
+
+FORESTS = small_forests()
+_SF = {}
+
+
+def sf_for(f):
+    if f.name not in _SF:
+        _SF[f.name] = StarForest.from_forest(f).setup()
+    return _SF[f.name]
+
+
+DT = ["int32", "int64", "fp32", "fp64", "bf16"]
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("path", ["fused", "three_phase", "root_major"])
+@pytest.mark.parametrize("op", ["REPLACE", "SUM", "MAX"])
+@pytest.mark.parametrize("dtype,bs", [("fp64", 1), ("int32", 1), ("fp32", 3), ("bf16", 8), ("int64", 2)])
+def test_bcast_bit_exact(f, path, op, dtype, bs):
+    sf = sf_for(f).set_path(path)
+    root, leaf = make_data(f, dtype, bs, 100)
+    want = oracle.bcast(f, dtype, bs, root, leaf, op)
+    r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+    sf.bcast(r, l, op, bs=bs)
+    assert_bits_equal(to_host(l, dtype), want, f"bcast {f.name} {path} {op} {dtype}x{bs}")
+    assert_bits_equal(to_host(r, dtype), root, "rootdata must be untouched")
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("op", ["REPLACE", "SUM", "MIN", "MAX"])
+@pytest.mark.parametrize("dtype", DT)
+def test_reduce_deterministic_bit_exact(f, op, dtype):
+    sf = sf_for(f).set_mode("deterministic")
+    for bs in (1, 5):
+        root, leaf = make_data(f, dtype, bs, 200)
+        want = oracle.reduce(f, dtype, bs, leaf, root, op)
+        r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+        sf.reduce(l, r, op, bs=bs)
+        assert_bits_equal(to_host(r, dtype), want, f"reduce det {f.name} {op} {dtype}x{bs}")
+        assert_bits_equal(to_host(l, dtype), leaf, "leafdata must be untouched")
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
+@pytest.mark.parametrize("dtype", ["int32", "int64", "fp32", "fp64"])
+def test_reduce_atomic(f, op, dtype):
+    sf = sf_for(f).set_mode("atomic")
+    bs = 2
+    root, leaf = make_data(f, dtype, bs, 300)
+    want = oracle.reduce(f, dtype, bs, leaf, root, op)
+    r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+    sf.reduce(l, r, op, bs=bs)
+    got = to_host(r, dtype)
+    sf.set_mode("deterministic")
+    if op == "SUM" and dtype.startswith("fp"):
+        assert_atomic_sum_close(got, want, f, dtype, bs, leaf, root, f"reduce atomic {f.name} {dtype}")
+    else:
+        assert_bits_equal(got, want, f"reduce atomic {f.name} {op} {dtype}")
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("op", ["SUM", "MAX", "REPLACE"])
+@pytest.mark.parametrize("dtype,bs", [("int32", 1), ("fp64", 1), ("fp32", 4), ("int64", 3)])
+def test_fetch_and_op_deterministic_bit_exact(f, op, dtype, bs):
+    sf = sf_for(f).set_mode("deterministic")
+    root, leaf = make_data(f, dtype, bs, 400)
+    upd0 = sfgen.data(dtype, leaf.size, 400, 3)
+    want_root, want_upd = oracle.fetch_and_op(f, dtype, bs, root, leaf, upd0, op)
+    r, l, u = to_dev(root, dtype), to_dev(leaf, dtype), to_dev(upd0, dtype)
+    sf.fetch_and_op(r, l, u, op, bs=bs)
+    assert_bits_equal(to_host(r, dtype), want_root, f"fetch root {f.name} {op}")
+    assert_bits_equal(to_host(u, dtype), want_upd, f"fetch leafupdate {f.name} {op}")
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("dtype", ["int32", "int64", "fp64"])
+def test_fetch_and_op_atomic_multisf(f, dtype):
+    """Atomic order is the hardware's: check the multi-SF invariant (Sec. III.B) and that the
+    fetched values of each root are its running sums in some order of its leaves."""
+    sf = sf_for(f).set_mode("atomic")
+    ro, lo = oracle.layout(f)
+    deg = oracle.in_degree(f)
+    npt = oracle.NPTYPE[dtype]
+    off = np.concatenate([[0], np.cumsum(deg)[:-1]]).astype(npt)
+    ones = np.ones(lo[-1], npt)
+    r, l, u = to_dev(off, dtype), to_dev(ones, dtype), to_dev(np.full(lo[-1], -1, npt), dtype)
+    sf.fetch_and_op(r, l, u, "SUM", bs=1)
+    sf.set_mode("deterministic")
+    assert np.array_equal(to_host(r, dtype), off + deg)
+    got_upd = to_host(u, dtype)
+    from tests import npref
+    L, R = npref.edge_arrays(f)
+    for root in np.unique(R)[:2000]:
+        fetched = np.sort(got_upd[L[R == root]])
+        assert np.array_equal(fetched, off[root] + np.arange(deg[root])), root
+
+
+def test_reduce_heavy_root_recursive_fold():
+    """A star of 300,000 leaves: 4688 blocks -> 74 -> 2 -> 1, three fold levels."""
+    n = 300000
+    f = sfgen.Forest(1, np.array([3]), np.array([n]), [None], [np.zeros(n, np.int32)],
+                     [(np.arange(n) % 7 == 0).astype(np.int64)], name="heavystar")
+    sf = StarForest.from_forest(f).setup()
+    for dtype in ("fp32", "fp64", "bf16"):
+        root, leaf = make_data(f, dtype, 1, 500)
+        want = oracle.reduce(f, dtype, 1, leaf, root, "SUM")
+        r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+        for _ in range(2):      # second call: the arrival counters must have been reset
+            r.copy_(to_dev(root, dtype))
+            sf.reduce(l, r, "SUM")
+            assert_bits_equal(to_host(r, dtype), want, f"heavy star {dtype}")
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_memtype_host_buffers(dtype):
+    f = sfgen.cfg1_plain_tiny()
+    sf = sf_for(f)
+    root, leaf = make_data(f, dtype, 1, 600)
+    want_b = oracle.bcast(f, dtype, 1, root, leaf, "REPLACE")
+    want_r = oracle.reduce(f, dtype, 1, leaf, root, "SUM")
+    rh = torch.from_numpy(root.copy()).pin_memory()
+    lh = torch.from_numpy(leaf.copy()).pin_memory()
+    sf.bcast_memtype(rh, lh, "REPLACE")
+    torch.cuda.synchronize()
+    assert_bits_equal(lh.numpy(), want_b, "bcast host")
+    lh2 = torch.from_numpy(leaf.copy()).pin_memory()
+    rh2 = torch.from_numpy(root.copy()).pin_memory()
+    sf.set_mode("deterministic")
+    sf.reduce_memtype(lh2, rh2, "SUM")
+    torch.cuda.synchronize()
+    assert_bits_equal(rh2.numpy(), want_r, "reduce host")
+
+
+def test_begin_end_protocol_errors():
+    f = sfgen.cfg1_plain_tiny()
+    sf = sf_for(f).set_path("three_phase")
+    root, leaf = make_data(f, "fp64", 1, 700)
+    r, l = to_dev(root, "fp64"), to_dev(leaf, "fp64")
+    sf.bcast_begin(r, l, "REPLACE")
+    with pytest.raises(SFError) as e:
+        sf.bcast_begin(r, l, "REPLACE")
+    assert e.value.name == "SF_ERR_PENDING"
+    with pytest.raises(SFError) as e:
+        sf.destroy()
+    assert e.value.name == "SF_ERR_PENDING"
+    # independent work between begin and end, then end completes the unpack
+    x = torch.ones(1000, device="cuda") * 2
+    sf.bcast_end(r, l, "REPLACE")
+    assert_bits_equal(to_host(l, "fp64"), oracle.bcast(f, "fp64", 1, root, leaf, "REPLACE"), "three-phase end")
+    with pytest.raises(SFError) as e:
+        sf.bcast_end(r, l, "REPLACE")
+    assert e.value.name == "SF_ERR_NO_PENDING"
+    sf.set_path("fused")
+    # two concurrent operations on one forest with different data (Sec. III.A)
+    l2 = to_dev(leaf, "fp64")
+    sf.bcast_begin(r, l, "REPLACE")
+    sf.bcast_begin(r, l2, "REPLACE")
+    sf.bcast_end(r, l2, "REPLACE")
+    sf.bcast_end(r, l, "REPLACE")
+    assert float(x.sum()) == 2000.0
+
+
+def test_misaligned_pointer_rejected():
+    f = sfgen.cfg1_plain_tiny()
+    sf = sf_for(f)
+    buf = torch.zeros(20000 * 8 + 1, dtype=torch.uint8, device="cuda")
+    lib = sf._lib
+    from paper_2102_13018_gb300 import _abi
+    import ctypes
+    u = _abi.sf_unit(_abi.SF_FP64, 1)
+    p = ctypes.c_void_p(buf.data_ptr() + 1)
+    assert lib.sf_bcast_begin(sf._h, u, p, p, 0, None) == _abi.CODES["SF_ERR_ALIGN"]
+
+
+def test_launch_counter_advances():
+    f = sfgen.fig2()
+    sf = sf_for(f)
+    root, leaf = make_data(f, "fp64", 1, 800)
+    n0 = launch_count()
+    sf.bcast(to_dev(root, "fp64"), to_dev(leaf, "fp64"))
+    assert launch_count() > n0
