@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Star-forest Bcast/Reduce benchmark on GB300 (one JSON line on rank 0).
+
+Workload (default): the unstructured SpMV-style scatter of Sec. IV.A -- 2^24 roots of a random
+geometric 3-D graph (expected degree 14) split into 256 simulated ranks by coordinate
+bisection; leaves are each rank's owned entries followed by its ghost columns; fp64 units of
+bs = 1.  One step is the SpMV communication pair: lvec = Bcast_REPLACE(x) and
+y = y + Reduce_SUM(lvec) (deterministic fold), both through the C ABI.
+
+value = algorithmic bytes of the step / device time (CUDA events on the launching stream,
+L2 flushed between steps by writing a 256 MiB buffer outside the timed events).
+Algorithmic bytes: Bcast reads each connected root once, writes every leaf, plus 4 bytes per
+index word the two-sided plan needs; Reduce reads every leaf, reads and writes each connected
+root once, plus the same index words.
+
+--impl reference times the oracle (plain C, single-threaded) on the host cores instead.
+Multi-GPU (torchrun): every rank runs an independent replica (the simulated ranks already
+live in one GPU's memory; nothing crosses GPUs), value = all replicas' bytes / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SF Bcast/Reduce effective HBM GB/s (% of peak); batched vs per-SF launch time"
+KERNEL_SOURCES = ["paper_2102_13018_gb300/csrc/sf_kernels.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--npoints", type=int, default=1 << 24)
+    ap.add_argument("--levels", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, forest):
+    return {
+        "workload": f"spmv_scatter: random geometric 3-D graph, {args.npoints} roots (degree 14), "
+                    f"{2 ** args.levels} simulated ranks by coordinate bisection, leaves = owned + "
+                    f"{forest.meta['ghosts']} ghost columns, fp64 bs=1; step = Bcast REPLACE + Reduce SUM "
+                    f"(deterministic)",
+        "roots": int(forest.nroots.sum()),
+        "leaves": int(forest.nedges),
+        "ranks": int(forest.nranks),
+        "l2": "flushed between steps (256 MiB write outside the timed events)",
+        "parallelism": "replicas (one independent forest per GPU)",
+    }
+
+
+def algorithmic_bytes(info, unit_bytes=8):
+    idx_words = info["edges_one_indexed"] + 2 * info["edges_two_indexed"]
+    bcast = unit_bytes * info["connected_roots"] + unit_bytes * info["nedges"] + 4 * idx_words
+    reduce = unit_bytes * info["nedges"] + 2 * unit_bytes * info["connected_roots"] + 4 * idx_words
+    return bcast, reduce
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (burst copy, MEASURED_PEAKS.json)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel
+    source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kernel)
+    if not ent or ent.get("source_sha") != kernel_source_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+        if dev.isdigit():
+            rows = [r for r in rows if r[0] == dev] or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_forest(args):
+    import sfgen
+    return sfgen.cfg3_spmv(args.npoints, args.levels)
+
+
+def oracle_step_time(forest, x, lvec, y, reps=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lv = oracle.bcast(forest, "fp64", 1, x, lvec, "REPLACE")
+        oracle.reduce(forest, "fp64", 1, lv, y, "SUM")
+    return (time.perf_counter() - t0) / reps
+
+
+def sample_forest(forest, keep):
+    """The forest restricted to the leaves of leaf ranks 0..keep-1 (all roots kept)."""
+    import numpy as np
+    import sfgen
+    P = forest.nranks
+    nl = np.array([forest.nleaves[q] if q < keep else 0 for q in range(P)])
+    il = [forest.ilocal[q] if q < keep else None for q in range(P)]
+    rr = [forest.iremote_rank[q] if q < keep else np.zeros(0, np.int32) for q in range(P)]
+    ri = [forest.iremote_index[q] if q < keep else np.zeros(0, np.int64) for q in range(P)]
+    return sfgen.Forest(P, forest.nroots, nl, il, rr, ri, name=forest.name + f"_first{keep}", meta=forest.meta)
+
+
+def run_reference(args):
+    import numpy as np
+    import oracle
+    import sfgen
+    forest = build_forest(args)
+    # bound the whole run to about two minutes of oracle time
+    budget = 120.0 / (args.steps + args.warmup)
+    ro, lo = oracle.layout(forest)
+    x = sfgen.data("fp64", int(ro[-1]), 3, 1)
+    y = sfgen.data("fp64", int(ro[-1]), 3, 2)
+    probe = sample_forest(forest, max(1, forest.nranks // 16))
+    t_probe = oracle_step_time(probe, x, np.zeros(int(oracle.layout(probe)[1][-1])), y)
+    est_full = t_probe * forest.nedges / max(probe.nedges, 1)
+    keep = forest.nranks if est_full <= budget else max(1, int(forest.nranks * budget / est_full))
+    sample = forest if keep == forest.nranks else sample_forest(forest, keep)
+    lvec = np.zeros(int(oracle.layout(sample)[1][-1]))
+    info = host_info(sample)
+    bb, rb = algorithmic_bytes(info)
+    for _ in range(args.warmup):
+        oracle_step_time(sample, x, lvec, y)
+    times = [oracle_step_time(sample, x, lvec, y) for _ in range(args.steps)]
+    total = sum(times)
+    value = (bb + rb) * args.steps / total / 1e9
+    what = ("the full workload" if keep == forest.nranks else
+            f"the leaves of the first {keep} of {forest.nranks} ranks ({sample.nedges} of {forest.nedges} edges)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, forest),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "GB/s",
+                             "sample": what + ", one Bcast REPLACE + one Reduce SUM per step"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def host_info(forest):
+    """Plan statistics from the library's host setup pass (no GPU needed)."""
+    from paper_2102_13018_gb300 import StarForest
+    return StarForest.from_forest(forest).analyze().info()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import sfgen
+    from paper_2102_13018_gb300 import StarForest, launch_count
+
+    forest = build_forest(args)
+    t0 = time.perf_counter()
+    sf = StarForest.from_forest(forest).setup()
+    setup_s = time.perf_counter() - t0
+    sf.set_mode("deterministic").set_path("fused")
+    info = sf.info()
+    nr, nl = sf.nroots_total, sf.leaf_extent
+    x_h = sfgen.data("fp64", nr, 3, 1)
+    y_h = sfgen.data("fp64", nr, 3, 2)
+    x = torch.from_numpy(x_h).cuda()
+    y = torch.from_numpy(y_h).cuda()
+    lvec = torch.zeros(nl, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sf.bcast(x, lvec, "REPLACE", stream=stream)
+        sf.reduce(lvec, y, "SUM", stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.2)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = launch_count()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        e = ev[i]
+        e[0].record(stream)
+        sf.bcast_begin(x, lvec, "REPLACE", stream=stream)
+        sf.bcast_end(x, lvec, "REPLACE", stream=stream)
+        e[1].record(stream)
+        sf.reduce_begin(lvec, y, "SUM", stream=stream)
+        sf.reduce_end(lvec, y, "SUM", stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    launches = launch_count() - n0
+    clk = clocks.stop()
+    bcast_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    reduce_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    total_ms = sum(bcast_ms) + sum(reduce_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    bb, rb = algorithmic_bytes(info)
+    value = world * (bb + rb) * K / (max_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
+    b_avg, r_avg = statistics.mean(bcast_ms), statistics.mean(reduce_ms)
+    dom = ("rm_kernel", rb, r_avg) if r_avg >= b_avg else ("ts_kernel", bb, b_avg)
+    achieved = dom[1] / (dom[2] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom[0] + (" (Reduce SUM, deterministic)" if dom[0] == "rm_kernel"
+                                                    else " (Bcast REPLACE, fused)"),
+                "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": committed_traffic(dom[0]),
+                "algorithmic_bytes_per_launch": dom[1]}
+    ops = {"bcast_ms": b_avg, "reduce_ms": r_avg, "bcast_gbs": bb / (b_avg * 1e-3) / 1e9,
+           "reduce_gbs": rb / (r_avg * 1e-3) / 1e9, "bcast_frac": bb / (b_avg * 1e-3) / 1e9 / peak,
+           "reduce_frac": rb / (r_avg * 1e-3) / 1e9 / peak, "bcast_bytes": bb, "reduce_bytes": rb,
+           "setup_s": setup_s, "host_wall_s": wall}
+
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_h).pin_memory()
+        yh = torch.from_numpy(y_h).pin_memory()
+        lh = torch.zeros(nl, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            sf.bcast_memtype(xh, lh, "REPLACE", stream=stream)
+            sf.reduce_memtype(lh, yh, "SUM", stream=stream)
+        torch.cuda.synchronize()
+        Ke = max(3, min(K, 50))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(Ke):
+            sf.bcast_memtype(xh, lh, "REPLACE", stream=stream)
+            sf.reduce_memtype(lh, yh, "SUM", stream=stream)
+            stream.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / Ke
+        # Bcast: x in (leaves are all written by REPLACE, so not copied in), lvec out;
+        # Reduce: lvec in, y in, y out
+        h2d = 8 * nr + 8 * nl + 8 * nr
+        d2h = 8 * nl + 8 * nr
+        e2e = {"value": world * (bb + rb) / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        lv0 = np.zeros(nl)
+        secs = oracle_step_time(forest, x_h, lv0, y_h, reps=1)
+        reps = max(1, min(10, int(20.0 / max(secs, 1e-3))))
+        secs = oracle_step_time(forest, x_h, lv0, y_h, reps=reps) if reps > 1 else secs
+        cpu = {"value": (bb + rb) / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the full workload, {reps} step(s) of one Bcast REPLACE + one Reduce SUM"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "ops": ops,
+                "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
+                                              "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
+                                              "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -192,8 +192,9 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
   if (path == SF_PATH_ROOT_MAJOR) {
     const int vb = pick_vb(w, ub, true, {root, leaf});
     if (!vb) return SF_ERR_ALIGN;
-    RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vb);
-    return launched(launch_rm(u.dtype, op, vb, RM_BCAST, a, sf->dp.n_rm_fold_tiles, s));
+    const int vbo = copy ? vb : (vb == 16 ? 16 : w);
+    RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vbo);
+    return launched(launch_rm(u.dtype, op, vbo, RM_BCAST, a, sf->dp.n_rm_fold_tiles, s));
   }
   if (path == SF_PATH_THREE_PHASE && sf->dp.remote_units > 0) {
     const size_t bytes = size_t(sf->dp.remote_units) * ub;
@@ -505,8 +506,11 @@ int sf_bcast_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t rootmtype, const
   }
   if (leafmtype == SF_MEM_HOST) {
     if ((rc = ensure(sf->stage_leaf, lb, false, s))) return rc;
-    // every op reads the leaves it leaves untouched back out, so the whole leaf array goes in
-    if (lb && (rc = cuda_err(cudaMemcpyAsync(sf->stage_leaf.p, leafdata, lb, cudaMemcpyHostToDevice, s)))) return rc;
+    // the whole leaf array goes back out, so it must come in unless REPLACE writes every slot
+    const bool all_written = op == SF_REPLACE && sf->info.nedges == sf->info.leaf_extent_total;
+    if (lb && !all_written &&
+        (rc = cuda_err(cudaMemcpyAsync(sf->stage_leaf.p, leafdata, lb, cudaMemcpyHostToDevice, s))))
+      return rc;
     dleaf = sf->stage_leaf.p;
   }
   int finish = 0;

@@ -40,7 +40,8 @@ DT = ["int32", "int64", "fp32", "fp64", "bf16"]
 @pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
 @pytest.mark.parametrize("path", ["fused", "three_phase", "root_major"])
 @pytest.mark.parametrize("op", ["REPLACE", "SUM", "MAX"])
-@pytest.mark.parametrize("dtype,bs", [("fp64", 1), ("int32", 1), ("fp32", 3), ("bf16", 8), ("int64", 2)])
+@pytest.mark.parametrize("dtype,bs", [("fp64", 1), ("int32", 1), ("fp32", 3), ("bf16", 8), ("int64", 2),
+                                      ("fp32", 2), ("bf16", 3)])
 def test_bcast_bit_exact(f, path, op, dtype, bs):
     sf = sf_for(f).set_path(path)
     root, leaf = make_data(f, dtype, bs, 100)
