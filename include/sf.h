@@ -196,6 +196,31 @@ int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, cons
 int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
                                int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
 
+/* Maximum scratch, in bytes, that sf_reduce_noalloc may use (a fixed device array). */
+#define SF_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Deterministic Reduce that allocates nothing.  The paper has no counterpart: this exists for
+ * callers that may not allocate device memory at the time of the call -- for example code
+ * that runs under a memory budget fixed at start-up, inside a custom allocator's callback, or
+ * next to a stream capture that must not see allocations.  sf_reduce_begin/end may grow the
+ * forest's fold scratch with cudaMalloc on the first operation with a wider unit; this call
+ * instead keeps the fold partials and arrival counters in one file-scope device array of
+ * SF_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until exit.
+ *
+ * Computes exactly what sf_reduce_begin + sf_reduce_end compute in SF_MODE_DETERMINISTIC
+ * (bit-identical results), whatever mode the forest is set to, and completes in one call
+ * (no End; nothing is left pending).  The forest must be set up (sf_setup); the caller
+ * passes leafdata and rootdata as for sf_reduce_begin.
+ * The first call on a device looks up the array's device address with cudaGetSymbolAddress
+ * (with that device current); make that first call before any stream capture.  Each call
+ * clears the counters it uses on `stream` before its kernel.  All calls share the one array:
+ * calls whose work overlaps on the GPU (different streams, or concurrent processes' threads
+ * on one context) race and give wrong results; serialise them.
+ * Errors: those of sf_reduce_begin, and SF_ERR_TOO_LARGE when the forest's fold scratch for
+ * this unit exceeds SF_NOALLOC_SCRATCH_BYTES (nothing is launched then). */
+int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                      sf_stream_t stream);
+
 /* Free the forest and its device plans.  SF_ERR_PENDING (and nothing freed) if a Begin has
  * no End yet.  Synchronises the device work the library enqueued before freeing. */
 int sf_destroy(sf_t *sf);

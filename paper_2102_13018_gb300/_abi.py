@@ -15,6 +15,7 @@ SF_MODE_AUTO, SF_MODE_ATOMIC, SF_MODE_DETERMINISTIC = range(3)
 SF_PATH_AUTO, SF_PATH_FUSED, SF_PATH_THREE_PHASE, SF_PATH_ROOT_MAJOR = range(4)
 SF_MEM_HOST, SF_MEM_DEVICE = 0, 1
 SF_FOLD_BLOCK = 64
+SF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 ERRORS = {0: "SF_SUCCESS", 1: "SF_ERR_ARG", 2: "SF_ERR_NULL", 3: "SF_ERR_RANGE", 4: "SF_ERR_DUP_LEAF",
           5: "SF_ERR_STATE", 6: "SF_ERR_NO_PENDING", 7: "SF_ERR_PENDING", 8: "SF_ERR_UNSUPPORTED",
@@ -86,6 +87,7 @@ def load():
     for name in ("sf_bcast_with_memtype_begin", "sf_bcast_with_memtype_end",
                  "sf_reduce_with_memtype_begin", "sf_reduce_with_memtype_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, i32, vp, i32, vp, i32, vp]
+    lib.sf_reduce_noalloc.argtypes = [vp, sf_unit, vp, vp, i32, vp]
     lib.sf_destroy.argtypes = [vp]
     lib.sf_error_string.argtypes = [ctypes.c_int]
     lib.sf_error_string.restype = ctypes.c_char_p

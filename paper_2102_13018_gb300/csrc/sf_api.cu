@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -617,3 +618,70 @@ const char *sf_error_string(int code) {
 int64_t sf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"
+
+// ---- deterministic Reduce without allocation ----------------------------------------------
+// The fold partials and arrival counters of sf_reduce_noalloc live in this fixed array instead
+// of the forest's cudaMalloc'd scratch.  Host code never uses the symbol itself (on the host it
+// is only a stand-in, not a device address): the device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(void **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return SF_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SF_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SF_SUCCESS;
+}
+}  // namespace
+
+extern "C" int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                                 sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  const int w = elem_size(unit.dtype), ub = w * unit.bs;
+  if ((sf->info.nroots_total && (rc = check_ptr(rootdata, w))) ||
+      (sf->info.leaf_extent_total && (rc = check_ptr(leafdata, w))))
+    return rc;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  const int vb = pick_vb(w, ub, true, {rootdata, leafdata});
+  if (!vb) return SF_ERR_ALIGN;
+  const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+  const int nv = ub / vbo;
+  // counters first (256-byte rounded), then the partials
+  size_t cbytes = 0, pbytes = 0;
+  if (op != SF_REPLACE) {
+    cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
+    pbytes = size_t(sf->dp.n_partial_slots) * nv * acc_pack_bytes(unit.dtype, op, vbo);
+  }
+  const size_t coff = 0, poff = (cbytes + 255) & ~size_t(255);
+  if (poff + pbytes > SF_NOALLOC_SCRATCH_BYTES) return SF_ERR_TOO_LARGE;
+  void *scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(scratch);
+  if (cbytes && (rc = cuda_err(cudaMemsetAsync(base + coff, 0, cbytes, s)))) return rc;
+  const Tile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+  RmArgs a = rm_args(sf, tiles, rootdata, const_cast<void *>(leafdata), nullptr, nv);
+  a.partial = base + poff;
+  a.counter = reinterpret_cast<int32_t *>(base + coff);
+  return launched(launch_rm(unit.dtype, op, vbo, RM_REDUCE, a, nt, s));
+}
