@@ -146,12 +146,13 @@ int launched(cudaError_t e) {
   return SF_SUCCESS;
 }
 
-TsArgs ts_args(const sf_t *sf, const Tile *tiles, const void *src, void *dst, void *upd, int nv, int phase) {
+TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *src, void *dst, void *upd, int nv,
+               int phase) {
   TsArgs a{};
-  a.runs = sf->dp.runs;
   a.ridx = sf->dp.ts_ridx;
   a.lidx = sf->dp.ts_lidx;
   a.tiles = tiles;
+  a.ntiles = ntiles;
   a.src = src;
   a.dst = dst;
   a.upd = upd;
@@ -160,20 +161,18 @@ TsArgs ts_args(const sf_t *sf, const Tile *tiles, const void *src, void *dst, vo
   return a;
 }
 
-RmArgs rm_args(sf_t *sf, const Tile *tiles, void *root, void *leaf, void *upd, int nv) {
+RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv) {
   RmArgs a{};
-  a.mruns = sf->dp.mruns;
   a.mask = sf->dp.mask;
   a.pr_root = sf->dp.pr_root;
   a.pr_leaf = sf->dp.pr_leaf;
   a.m_root = sf->dp.m_root;
   a.m_ptr = sf->dp.m_ptr;
   a.m_leaf = sf->dp.m_leaf;
-  a.m_slot = sf->dp.m_slot;
-  a.m_ctr = sf->dp.m_ctr;
-  a.ch_m = sf->dp.ch_m;
-  a.ch_e0 = sf->dp.ch_e0;
+  a.blocks = sf->dp.blocks;
+  a.combs = sf->dp.combs;
   a.tiles = tiles;
+  a.ntiles = ntiles;
   a.root = root;
   a.leaf = leaf;
   a.upd = upd;
@@ -194,7 +193,7 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
     const int vb = pick_vb(w, ub, true, {root, leaf});
     if (!vb) return SF_ERR_ALIGN;
     const int vbo = copy ? vb : (vb == 16 ? 16 : w);
-    RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vbo);
+    RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, sf->dp.n_rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vbo);
     return launched(launch_rm(u.dtype, op, vbo, RM_BCAST, a, sf->dp.n_rm_fold_tiles, s));
   }
   if (path == SF_PATH_THREE_PHASE && sf->dp.remote_units > 0) {
@@ -205,10 +204,11 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
     if (!vb) return SF_ERR_ALIGN;
     const int nv = ub / vb;
     // self edges: direct scatter; remote edges: pack, then move
-    TsArgs self = ts_args(sf, sf->dp.ts_self_tiles, root, leaf, nullptr, nv, PH_FUSED);
+    TsArgs self = ts_args(sf, sf->dp.ts_self_tiles, sf->dp.n_ts_self_tiles, root, leaf, nullptr, nv, PH_FUSED);
     if ((rc = launched(launch_ts(u.dtype, op, vb, false, false, false, self, sf->dp.n_ts_self_tiles, s)))) return rc;
     const int vbc = pick_vb(w, ub, true, {root, sf->rootbuf.p, sf->leafbuf.p});
-    TsArgs pack = ts_args(sf, sf->dp.ts_remote_tiles, root, sf->rootbuf.p, nullptr, ub / vbc, PH_PACK);
+    TsArgs pack = ts_args(sf, sf->dp.ts_remote_tiles, sf->dp.n_ts_remote_tiles, root, sf->rootbuf.p, nullptr, ub / vbc,
+                          PH_PACK);
     if ((rc = launched(launch_ts(u.dtype, SF_REPLACE, vbc, false, false, false, pack, sf->dp.n_ts_remote_tiles, s))))
       return rc;
     MoveArgs mv{sf->dp.segs, sf->move_tiles, sf->rootbuf.p, sf->leafbuf.p, ub / vbc, 0};
@@ -219,7 +219,7 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
   const int vb = pick_vb(w, ub, true, {root, leaf});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = copy ? vb : (vb == 16 ? 16 : w);
-  TsArgs a = ts_args(sf, sf->dp.ts_tiles, root, leaf, nullptr, ub / vbo, PH_FUSED);
+  TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, root, leaf, nullptr, ub / vbo, PH_FUSED);
   return launched(launch_ts(u.dtype, op, vbo, false, false, false, a, sf->dp.n_ts_tiles, s));
 }
 
@@ -228,7 +228,8 @@ int bcast_finish(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
   const int vb = pick_vb(w, ub, op == SF_REPLACE, {leaf, sf->leafbuf.p});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
-  TsArgs a = ts_args(sf, sf->dp.ts_remote_tiles, sf->leafbuf.p, leaf, nullptr, ub / vbo, PH_UNPACK);
+  TsArgs a = ts_args(sf, sf->dp.ts_remote_tiles, sf->dp.n_ts_remote_tiles, sf->leafbuf.p, leaf, nullptr, ub / vbo,
+                     PH_UNPACK);
   return launched(launch_ts(u.dtype, op, vbo, false, false, false, a, sf->dp.n_ts_remote_tiles, s));
 }
 
@@ -238,7 +239,7 @@ int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int3
   if (sf->info.nedges == 0) return SF_SUCCESS;
   const bool atomic = sf->mode == SF_MODE_ATOMIC && op != SF_REPLACE && u.dtype != SF_BF16;
   if (atomic) {
-    TsArgs a = ts_args(sf, sf->dp.ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
+    TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
     return launched(launch_ts(u.dtype, op, w, true, true, false, a, sf->dp.n_ts_tiles, s));
   }
   const int vb = pick_vb(w, ub, true, {root, leaf});
@@ -251,9 +252,9 @@ int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int3
     const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
     if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
   }
-  const Tile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
+  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
   const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
-  RmArgs a = rm_args(sf, tiles, root, const_cast<void *>(leaf), nullptr, nv);
+  RmArgs a = rm_args(sf, tiles, nt, root, const_cast<void *>(leaf), nullptr, nv);
   return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, a, nt, s));
 }
 
@@ -263,13 +264,13 @@ int fetch_launch(sf_t *sf, const sf_unit &u, void *root, const void *leaf, void 
   if (sf->info.nedges == 0) return SF_SUCCESS;
   if (sf->mode == SF_MODE_ATOMIC) {
     if (u.bs != 1) return SF_ERR_UNSUPPORTED;
-    TsArgs a = ts_args(sf, sf->dp.ts_tiles, leaf, root, upd, 1, PH_FUSED);
+    TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, root, upd, 1, PH_FUSED);
     return launched(launch_ts(u.dtype, op, w, true, true, true, a, sf->dp.n_ts_tiles, s));
   }
   const int vb = pick_vb(w, ub, true, {root, leaf, upd});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
-  RmArgs a = rm_args(sf, sf->dp.rm_fetch_tiles, root, const_cast<void *>(leaf), upd, ub / vbo);
+  RmArgs a = rm_args(sf, sf->dp.rm_fetch_tiles, sf->dp.n_rm_fetch_tiles, root, const_cast<void *>(leaf), upd, ub / vbo);
   return launched(launch_rm(u.dtype, op, vbo, RM_FETCH, a, sf->dp.n_rm_fetch_tiles, s));
 }
 
@@ -324,12 +325,12 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
     for (int64_t k0 = 0; k0 < h.segs[i].n; k0 += 4096)
       sf->h_move_tiles.push_back(Tile{T_RUN, int32_t(i), int32_t(k0), int32_t(std::min<int64_t>(4096, h.segs[i].n - k0))});
   BlobBuilder b;
-  const size_t o_runs = b.add(h.runs), o_ridx = b.add(h.ts_ridx), o_lidx = b.add(h.ts_lidx),
+  const size_t o_ridx = b.add(h.ts_ridx), o_lidx = b.add(h.ts_lidx),
                o_tst = b.add(h.ts_tiles), o_tss = b.add(h.ts_self_tiles), o_tsr = b.add(h.ts_remote_tiles),
-               o_segs = b.add(h.segs), o_mv = b.add(sf->h_move_tiles), o_mr = b.add(h.mruns), o_mask = b.add(h.mask),
+               o_segs = b.add(h.segs), o_mv = b.add(sf->h_move_tiles), o_mask = b.add(h.mask),
                o_prr = b.add(h.pr_root), o_prl = b.add(h.pr_leaf), o_mro = b.add(h.m_root), o_mpt = b.add(h.m_ptr),
-               o_mle = b.add(h.m_leaf), o_msl = b.add(h.m_slot), o_mct = b.add(h.m_ctr), o_chm = b.add(h.ch_m),
-               o_che = b.add(h.ch_e0), o_rf = b.add(h.rm_fold_tiles), o_rw = b.add(h.rm_winner_tiles),
+               o_mle = b.add(h.m_leaf), o_blk = b.add(h.blocks), o_cmb = b.add(h.combs),
+               o_rf = b.add(h.rm_fold_tiles), o_rw = b.add(h.rm_winner_tiles),
                o_rfe = b.add(h.rm_fetch_tiles);
   const size_t bytes = std::max<size_t>(b.host.size(), 256);
   if (cudaMalloc(&sf->blob.p, bytes) != cudaSuccess) {
@@ -342,12 +343,11 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   if (cudaStreamSynchronize(s) != cudaSuccess) return SF_ERR_CUDA;
   char *base = static_cast<char *>(sf->blob.p);
   DevPlan &d = sf->dp;
-  d.runs = reinterpret_cast<const Run *>(base + o_runs);
   d.ts_ridx = reinterpret_cast<const int32_t *>(base + o_ridx);
   d.ts_lidx = reinterpret_cast<const int32_t *>(base + o_lidx);
-  d.ts_tiles = reinterpret_cast<const Tile *>(base + o_tst);
-  d.ts_self_tiles = reinterpret_cast<const Tile *>(base + o_tss);
-  d.ts_remote_tiles = reinterpret_cast<const Tile *>(base + o_tsr);
+  d.ts_tiles = reinterpret_cast<const TsTile *>(base + o_tst);
+  d.ts_self_tiles = reinterpret_cast<const TsTile *>(base + o_tss);
+  d.ts_remote_tiles = reinterpret_cast<const TsTile *>(base + o_tsr);
   d.segs = reinterpret_cast<const SegCopy *>(base + o_segs);
   d.n_ts_tiles = int32_t(h.ts_tiles.size());
   d.n_ts_self_tiles = int32_t(h.ts_self_tiles.size());
@@ -356,20 +356,17 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.remote_units = h.remote_units;
   sf->move_tiles = reinterpret_cast<const Tile *>(base + o_mv);
   sf->n_move_tiles = int32_t(sf->h_move_tiles.size());
-  d.mruns = reinterpret_cast<const MaskedRun *>(base + o_mr);
   d.mask = reinterpret_cast<const uint32_t *>(base + o_mask);
   d.pr_root = reinterpret_cast<const int32_t *>(base + o_prr);
   d.pr_leaf = reinterpret_cast<const int32_t *>(base + o_prl);
   d.m_root = reinterpret_cast<const int32_t *>(base + o_mro);
   d.m_ptr = reinterpret_cast<const int32_t *>(base + o_mpt);
   d.m_leaf = reinterpret_cast<const int32_t *>(base + o_mle);
-  d.m_slot = reinterpret_cast<const int32_t *>(base + o_msl);
-  d.m_ctr = reinterpret_cast<const int32_t *>(base + o_mct);
-  d.ch_m = reinterpret_cast<const int32_t *>(base + o_chm);
-  d.ch_e0 = reinterpret_cast<const int32_t *>(base + o_che);
-  d.rm_fold_tiles = reinterpret_cast<const Tile *>(base + o_rf);
-  d.rm_winner_tiles = reinterpret_cast<const Tile *>(base + o_rw);
-  d.rm_fetch_tiles = reinterpret_cast<const Tile *>(base + o_rfe);
+  d.blocks = reinterpret_cast<const Block *>(base + o_blk);
+  d.combs = reinterpret_cast<const Comb *>(base + o_cmb);
+  d.rm_fold_tiles = reinterpret_cast<const RmTile *>(base + o_rf);
+  d.rm_winner_tiles = reinterpret_cast<const RmTile *>(base + o_rw);
+  d.rm_fetch_tiles = reinterpret_cast<const RmTile *>(base + o_rfe);
   d.n_rm_fold_tiles = int32_t(h.rm_fold_tiles.size());
   d.n_rm_winner_tiles = int32_t(h.rm_winner_tiles.size());
   d.n_rm_fetch_tiles = int32_t(h.rm_fetch_tiles.size());
@@ -678,9 +675,9 @@ extern "C" int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(scratch);
   if (cbytes && (rc = cuda_err(cudaMemsetAsync(base + coff, 0, cbytes, s)))) return rc;
-  const Tile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
+  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
   const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
-  RmArgs a = rm_args(sf, tiles, rootdata, const_cast<void *>(leafdata), nullptr, nv);
+  RmArgs a = rm_args(sf, tiles, nt, rootdata, const_cast<void *>(leafdata), nullptr, nv);
   a.partial = base + poff;
   a.counter = reinterpret_cast<int32_t *>(base + coff);
   return launched(launch_rm(unit.dtype, op, vbo, RM_REDUCE, a, nt, s));

@@ -24,15 +24,17 @@ struct Graph {
 struct HostPlan {
   std::vector<Run> runs;
   std::vector<int32_t> ts_ridx, ts_lidx;
-  std::vector<Tile> ts_tiles, ts_self_tiles, ts_remote_tiles;
+  std::vector<TsTile> ts_tiles, ts_self_tiles, ts_remote_tiles;
   std::vector<SegCopy> segs;
   int64_t remote_units = 0;
 
   std::vector<MaskedRun> mruns;
   std::vector<uint32_t> mask;
   std::vector<int32_t> pr_root, pr_leaf;
-  std::vector<int32_t> m_root, m_ptr, m_leaf, m_slot, m_ctr, ch_m, ch_e0;
-  std::vector<Tile> rm_fold_tiles, rm_winner_tiles, rm_fetch_tiles;
+  std::vector<int32_t> m_root, m_ptr, m_leaf;
+  std::vector<Block> blocks;
+  std::vector<Comb> combs;
+  std::vector<RmTile> rm_fold_tiles, rm_winner_tiles, rm_fetch_tiles;
   int32_t n_partial_slots = 0, n_counters = 0;
 };
 

@@ -199,9 +199,9 @@ __device__ __forceinline__ int64_t pattern_unit(int64_t base, int64_t sy, int64_
 }
 
 struct TsArgs {
-  const Run *runs;
   const int32_t *ridx, *lidx;
-  const Tile *tiles;
+  const TsTile *tiles;
+  int32_t ntiles;
   const void *src;      // Bcast: rootdata (fused/pack) or leaf buffer (unpack); Reduce: leafdata / root buffer
   void *dst;            // Bcast: leafdata (fused/unpack) or root buffer (pack); Reduce: rootdata / leaf buffer
   void *upd;            // FetchAndOp: leafupdate
@@ -209,13 +209,124 @@ struct TsArgs {
   int32_t phase;        // PH_*
 };
 
+// Contiguous tile, copy: n bytes from s to d.  Both are aligned to `gran` bytes; 16-byte
+// vectors carry the body whenever s and d share their offset modulo 16.
+template <int GRAN>
+__device__ __forceinline__ void copy_contiguous(const char *s, char *d, int64_t n) {
+  using G = typename Raw<GRAN>::type;
+  const bool v16 = GRAN == 16 || ((reinterpret_cast<uintptr_t>(s) ^ reinterpret_cast<uintptr_t>(d)) & 15) == 0;
+  if (!v16) {
+    // s and d disagree modulo 16: GRAN-sized accesses, 8 in flight per thread
+    constexpr int UG = 8;
+    const G *sg = reinterpret_cast<const G *>(s);
+    G *dg = reinterpret_cast<G *>(d);
+    const int64_t ng = n / GRAN;
+    for (int64_t base = threadIdx.x; base < ng; base += int64_t(kThreads) * UG) {
+      G x[UG];
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (base + u * kThreads < ng) x[u] = sg[base + u * kThreads];
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (base + u * kThreads < ng) dg[base + u * kThreads] = x[u];
+    }
+    return;
+  }
+  // head up to the first 16-byte boundary of d, 16-byte body, tail: head and tail in GRAN units
+  const int64_t align_gap = int64_t((16 - (reinterpret_cast<uintptr_t>(d) & 15)) & 15);
+  const int64_t head = GRAN == 16 ? 0 : (n < align_gap ? n : align_gap);
+  const int64_t body = ((n - head) / 16) * 16;
+  for (int64_t i = threadIdx.x; i < head / GRAN; i += kThreads)
+    reinterpret_cast<G *>(d)[i] = reinterpret_cast<const G *>(s)[i];
+  for (int64_t i = (head + body) / GRAN + threadIdx.x; i < n / GRAN; i += kThreads)
+    reinterpret_cast<G *>(d)[i] = reinterpret_cast<const G *>(s)[i];
+  constexpr int U = 4;
+  const uint4 *sv = reinterpret_cast<const uint4 *>(s + head);
+  uint4 *dv = reinterpret_cast<uint4 *>(d + head);
+  const int64_t nb = body / 16;
+  for (int64_t base = threadIdx.x; base < nb; base += int64_t(kThreads) * U) {
+    uint4 x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * kThreads < nb) x[u] = sv[base + u * kThreads];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (base + u * kThreads < nb) dv[base + u * kThreads] = x[u];
+  }
+}
+
 // One CTA per tile of a TS run.  L2R = leaf -> root (Reduce / FetchAndOp), else root -> leaf.
+// Tile-uniform paths: contiguous on both sides (a copy or an element-wise op), contiguous
+// destination with an indexed source (a gather), and the general multi-strided / indexed case.
 template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
-__global__ void __launch_bounds__(kThreads) ts_kernel(TsArgs a) {
-  const Tile t = a.tiles[blockIdx.x];
-  const Run r = a.runs[t.a];
+__device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &r) {
+  const TsTile &t = r;
   const bool flat = r.nx >= r.n;
   const int32_t nv = a.nv;
+  const bool ridx = r.flags & RUN_ROOT_IDX, lidx = r.flags & RUN_LEAF_IDX;
+  // source / destination side descriptions
+  bool s_idx = L2R ? lidx : ridx, d_idx = L2R ? ridx : lidx;
+  bool s_flat = flat && !s_idx, d_flat = flat && !d_idx;
+  int64_t s0 = L2R ? r.leaf0 : r.root0, d0 = L2R ? r.root0 : r.leaf0;
+  if (a.phase == PH_PACK) { d_flat = true; d_idx = false; d0 = L2R ? r.lbuf0 : r.rbuf0; }
+  if (a.phase == PH_UNPACK) { s_flat = true; s_idx = false; s0 = L2R ? r.rbuf0 : r.lbuf0; }
+  if constexpr (!ATOMIC) {
+    if (s_flat && d_flat) {
+      if constexpr (OP == OP_REPLACE) {
+        copy_contiguous<VB>(static_cast<const char *>(a.src) + (s0 + t.k0) * nv * VB,
+                            static_cast<char *>(a.dst) + (d0 + t.k0) * nv * VB, int64_t(t.cnt) * nv * VB);
+      } else {
+        const int64_t nvec = int64_t(t.cnt) * nv, sb = (s0 + t.k0) * nv, db = (d0 + t.k0) * nv;
+        for (int64_t base = threadIdx.x; base < nvec; base += int64_t(kThreads) * kUnroll) {
+          Pack<T, VB> x[kUnroll], y[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u)
+            if (base + u * kThreads < nvec) {
+              x[u] = ld<T, VB>(a.src, sb + base + u * kThreads);
+              y[u] = ld<T, VB>(a.dst, db + base + u * kThreads);
+            }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u)
+            if (base + u * kThreads < nvec) st<T, VB>(a.dst, db + base + u * kThreads, combine<OP, T, VB>(y[u], x[u]));
+        }
+      }
+      return;
+    }
+    if (d_flat && s_idx) {
+      // gather: destination contiguous, source through the index array
+      const int32_t *sidx = (L2R ? a.lidx : a.ridx) + r.idx0 + t.k0;
+      const int64_t db = (d0 + t.k0) * nv;
+      const int32_t nvec = t.cnt * nv;
+      constexpr int UG = VB >= 16 ? 4 : 8;
+      for (int32_t base = threadIdx.x; base < nvec; base += kThreads * UG) {
+        int64_t su[UG];
+        Pack<T, VB> x[UG];
+#pragma unroll
+        for (int u = 0; u < UG; ++u) {
+          const int32_t w = base + u * kThreads;
+          const int32_t k = nv == 1 ? w : w / nv;
+          su[u] = w < nvec ? int64_t(__ldg(sidx + k)) * nv + (w - k * nv) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          if (base + u * kThreads < nvec) x[u] = ld<T, VB>(a.src, su[u]);
+        if constexpr (OP == OP_REPLACE) {
+#pragma unroll
+          for (int u = 0; u < UG; ++u)
+            if (base + u * kThreads < nvec) st<T, VB>(a.dst, db + base + u * kThreads, x[u]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < UG; ++u)
+            if (base + u * kThreads < nvec) {
+              const int64_t di = db + base + u * kThreads;
+              st<T, VB>(a.dst, di, combine<OP, T, VB>(ld<T, VB>(a.dst, di), x[u]));
+            }
+        }
+      }
+      return;
+    }
+  }
+  // general: pattern or index on either side
   const int64_t work = int64_t(t.cnt) * nv;
   for (int64_t base = threadIdx.x; base < work; base += int64_t(kThreads) * kUnroll) {
     int64_t su[kUnroll], du[kUnroll], lu[kUnroll];
@@ -228,10 +339,8 @@ __global__ void __launch_bounds__(kThreads) ts_kernel(TsArgs a) {
       const int32_t kl = ok[u] ? int32_t(w / nv) : 0;
       vv[u] = ok[u] ? int32_t(w - int64_t(kl) * nv) : 0;
       const int32_t k = t.k0 + kl;
-      const int64_t ru = (r.flags & RUN_ROOT_IDX) ? int64_t(a.ridx[r.idx0 + k])
-                                                  : pattern_unit(r.root0, r.rsy, r.rsz, k, r.nx, r.ny, flat);
-      const int64_t leafu = (r.flags & RUN_LEAF_IDX) ? int64_t(a.lidx[r.idx0 + k])
-                                                     : pattern_unit(r.leaf0, r.lsy, r.lsz, k, r.nx, r.ny, flat);
+      const int64_t ru = ridx ? int64_t(a.ridx[r.idx0 + k]) : pattern_unit(r.root0, r.rsy, r.rsz, k, r.nx, r.ny, flat);
+      const int64_t leafu = lidx ? int64_t(a.lidx[r.idx0 + k]) : pattern_unit(r.leaf0, r.lsy, r.lsz, k, r.nx, r.ny, flat);
       int64_t s = L2R ? leafu : ru, d = L2R ? ru : leafu;
       if (a.phase == PH_PACK) d = (L2R ? r.lbuf0 : r.rbuf0) + k;
       if (a.phase == PH_UNPACK) s = (L2R ? r.rbuf0 : r.lbuf0) + k;
@@ -270,6 +379,20 @@ __global__ void __launch_bounds__(kThreads) ts_kernel(TsArgs a) {
   }
 }
 
+// Resident CTAs per SM the register budget must allow: copies are lean, op kernels carry
+// arithmetic and more live state.
+template <int OP, int VB> struct MinBlocks {
+  static constexpr int value = OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 4);
+};
+
+// One CTA per tile (the hardware balances uneven tiles); the tile carries its run inline so a
+// single descriptor load precedes the data.
+template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB>::value)) ts_kernel(TsArgs a) {
+  const TsTile t = a.tiles[blockIdx.x];
+  ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
+}
+
 // Buffer move: one CTA per slice of a (root rank -> leaf rank) chunk.
 struct MoveArgs {
   const SegCopy *segs;
@@ -305,11 +428,13 @@ __global__ void __launch_bounds__(kThreads) move_kernel(MoveArgs a) {
 
 // ------------------------------------------------------------------ root-major kernel
 struct RmArgs {
-  const MaskedRun *mruns;
   const uint32_t *mask;
   const int32_t *pr_root, *pr_leaf;
-  const int32_t *m_root, *m_ptr, *m_leaf, *m_slot, *m_ctr, *ch_m, *ch_e0;
-  const Tile *tiles;
+  const int32_t *m_root, *m_ptr, *m_leaf;
+  const Block *blocks;
+  const Comb *combs;
+  const RmTile *tiles;
+  int32_t ntiles;
   void *root;           // rootdata (read for Bcast, read-modify-write otherwise)
   void *leaf;           // leafdata (read for Reduce / FetchAndOp, read-modify-write for Bcast)
   void *upd;            // leafupdate (FetchAndOp)
@@ -337,56 +462,85 @@ __device__ Pack<A, VB> fold_partials(void *partial, int64_t slot, int32_t nv, in
   return acc;
 }
 
+// One single-leaf edge (root unit ru, leaf unit lu), vector v, all loads issued by the caller.
 template <typename T, int VB, int OP, int MODE>
-__device__ __forceinline__ void single_edge(const RmArgs &a, int64_t ru, int64_t leafu, int32_t v) {
-  const int64_t ri = ru * a.nv + v, li = leafu * a.nv + v;
+__device__ __forceinline__ void single_store(const RmArgs &a, int64_t ri, int64_t li, const Pack<T, VB> &x,
+                                             const Pack<T, VB> &y) {
+  // x = root vector, y = leaf vector (as loaded; unused ones are ignored)
   if constexpr (MODE == RM_BCAST) {
-    const Pack<T, VB> x = ld<T, VB>(a.root, ri);
     if constexpr (OP == OP_REPLACE) st<T, VB>(a.leaf, li, x);
-    else st<T, VB>(a.leaf, li, combine<OP, T, VB>(ld<T, VB>(a.leaf, li), x));
+    else st<T, VB>(a.leaf, li, combine<OP, T, VB>(y, x));
   } else if constexpr (MODE == RM_REDUCE) {
-    const Pack<T, VB> y = ld<T, VB>(a.leaf, li);
     if constexpr (OP == OP_REPLACE) st<T, VB>(a.root, ri, y);
-    else st<T, VB>(a.root, ri, combine<OP, T, VB>(ld<T, VB>(a.root, ri), y));
+    else st<T, VB>(a.root, ri, combine<OP, T, VB>(x, y));
   } else {
-    const Pack<T, VB> y = ld<T, VB>(a.leaf, li);
-    const Pack<T, VB> x = ld<T, VB>(a.root, ri);
     st<T, VB>(a.upd, li, x);
     st<T, VB>(a.root, ri, combine<OP, T, VB>(x, y));
   }
 }
 
+// Which vectors a single-leaf edge must read: the root unless Reduce REPLACE, the leaf unless
+// Bcast REPLACE.
+template <int OP, int MODE> struct SingleReads {
+  static constexpr bool root = !(MODE == RM_REDUCE && OP == OP_REPLACE);
+  static constexpr bool leaf = !(MODE == RM_BCAST && OP == OP_REPLACE);
+};
+
 template <typename T, int VB, int OP, int MODE>
-__global__ void __launch_bounds__(kThreads) rm_kernel(RmArgs a) {
+__device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;   // accumulator pack bytes
-  const Tile t = a.tiles[blockIdx.x];
+  constexpr int U = VB >= 16 ? 2 : 4;
   const int32_t nv = a.nv;
-  const int64_t work = int64_t(t.cnt) * nv;
-  if (t.kind == T_MASKED) {
-    const MaskedRun mr = a.mruns[t.a];
-    for (int64_t w = threadIdx.x; w < work; w += kThreads) {
-      const int32_t kl = int32_t(w / nv), v = int32_t(w - int64_t(kl) * nv), k = t.k0 + kl;
-      const int64_t bit = mr.mask0 + k;
-      if ((a.mask[bit >> 5] >> (bit & 31)) & 1u) single_edge<T, VB, OP, MODE>(a, mr.root0 + k, mr.leaf0 + k, v);
-    }
-  } else if (t.kind == T_PAIRS) {
-    for (int64_t w = threadIdx.x; w < work; w += kThreads) {
-      const int32_t kl = int32_t(w / nv), v = int32_t(w - int64_t(kl) * nv), i = t.a + kl;
-      single_edge<T, VB, OP, MODE>(a, a.pr_root[i], a.pr_leaf[i], v);
+  const int32_t work = t.cnt * nv;
+  if (t.kind == T_MASKED || t.kind == T_PAIRS) {
+    const RmTile &mr = t;
+    for (int32_t base = threadIdx.x; base < work; base += kThreads * U) {
+      int64_t ri[U], li[U];
+      bool on[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t w = base + u * kThreads;
+        const int32_t kl = nv == 1 ? w : w / nv, v = w - kl * nv;
+        on[u] = w < work;
+        int64_t ru = 0, lu = 0;
+        if (on[u]) {
+          if (t.kind == T_MASKED) {
+            const int64_t bit = mr.mask0 + t.k0 + kl;
+            on[u] = (__ldg(a.mask + (bit >> 5)) >> (bit & 31)) & 1u;
+            ru = mr.root0 + t.k0 + kl;
+            lu = mr.leaf0 + t.k0 + kl;
+          } else {
+            ru = __ldg(a.pr_root + t.a + kl);
+            lu = __ldg(a.pr_leaf + t.a + kl);
+          }
+        }
+        ri[u] = ru * nv + v;
+        li[u] = lu * nv + v;
+      }
+      Pack<T, VB> x[U], y[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (on[u]) {
+          if constexpr (SingleReads<OP, MODE>::root) x[u] = ld<T, VB>(a.root, ri[u]);
+          if constexpr (SingleReads<OP, MODE>::leaf) y[u] = ld<T, VB>(a.leaf, li[u]);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (on[u]) single_store<T, VB, OP, MODE>(a, ri[u], li[u], x[u], y[u]);
     }
   } else if (t.kind == T_WINNERS) {
     if constexpr (MODE == RM_REDUCE && OP == OP_REPLACE) {
-      for (int64_t w = threadIdx.x; w < work; w += kThreads) {
-        const int32_t kl = int32_t(w / nv), v = int32_t(w - int64_t(kl) * nv), m = t.a + kl;
+      for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+        const int32_t kl = w / nv, v = w - kl * nv, m = t.a + kl;
         const int64_t last = a.m_leaf[a.m_ptr[m + 1] - 1];
         st<T, VB>(a.root, int64_t(a.m_root[m]) * nv + v, ld<T, VB>(a.leaf, last * nv + v));
       }
     }
   } else if (t.kind == T_FETCH) {
     if constexpr (MODE == RM_FETCH) {
-      for (int64_t w = threadIdx.x; w < work; w += kThreads) {
-        const int32_t kl = int32_t(w / nv), v = int32_t(w - int64_t(kl) * nv), m = t.a + kl;
+      for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+        const int32_t kl = w / nv, v = w - kl * nv, m = t.a + kl;
         const int64_t ri = int64_t(a.m_root[m]) * nv + v;
         Pack<T, VB> x = ld<T, VB>(a.root, ri);
         const int32_t e1 = a.m_ptr[m + 1];
@@ -400,65 +554,91 @@ __global__ void __launch_bounds__(kThreads) rm_kernel(RmArgs a) {
       }
     }
   } else if (t.kind == T_CHUNKS) {
-    for (int64_t w = threadIdx.x; w < work; w += kThreads) {
-      const int32_t cl = int32_t(w / nv), v = int32_t(w - int64_t(cl) * nv), c = t.a + cl;
-      const int32_t m = a.ch_m[c], e0 = a.ch_e0[c], mp0 = a.m_ptr[m], mp1 = a.m_ptr[m + 1];
-      const int32_t e1 = min(e0 + FOLD_BLOCK, mp1);
-      const int64_t ri = int64_t(a.m_root[m]) * nv + v;
+    for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+      const int32_t cl = nv == 1 ? w : w / nv, v = w - cl * nv;
+      const Block b = a.blocks[t.a + cl];
+      const int64_t ri = int64_t(b.root) * nv + v;
+      const int32_t *lidx = a.m_leaf + b.e0;
       if constexpr (MODE == RM_BCAST) {
         const Pack<T, VB> x = ld<T, VB>(a.root, ri);
-        for (int32_t e = e0; e < e1; ++e) {
-          const int64_t li = int64_t(a.m_leaf[e]) * nv + v;
-          if constexpr (OP == OP_REPLACE) st<T, VB>(a.leaf, li, x);
-          else st<T, VB>(a.leaf, li, combine<OP, T, VB>(ld<T, VB>(a.leaf, li), x));
+        for (int32_t e = 0; e < b.n; e += U) {
+          int64_t li[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) li[u] = e + u < b.n ? int64_t(__ldg(lidx + e + u)) * nv + v : 0;
+          if constexpr (OP == OP_REPLACE) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (e + u < b.n) st<T, VB>(a.leaf, li[u], x);
+          } else {
+            Pack<T, VB> y[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (e + u < b.n) y[u] = ld<T, VB>(a.leaf, li[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (e + u < b.n) st<T, VB>(a.leaf, li[u], combine<OP, T, VB>(y[u], x));
+          }
         }
       } else if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
-        // left fold of this block in canonical order, 4 leaves in flight
+        // left fold of this block in canonical order, U leaves in flight
+        Pack<T, VB> xr;
+        if (b.comb < 0) xr = ld<T, VB>(a.root, ri);   // issued early: independent of the fold
         Pack<A, AVB> acc;
+        int32_t e = 0;
         {
-          const Pack<T, VB> y = ld<T, VB>(a.leaf, int64_t(a.m_leaf[e0]) * nv + v);
+          Pack<T, VB> y[U];
 #pragma unroll
-          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = to_acc<A, T>(y.v[l]);
+          for (int u = 0; u < U; ++u)
+            if (u < b.n) y[u] = ld<T, VB>(a.leaf, int64_t(__ldg(lidx + u)) * nv + v);
+#pragma unroll
+          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = to_acc<A, T>(y[0].v[l]);
+#pragma unroll
+          for (int u = 1; u < U; ++u)
+            if (u < b.n)
+#pragma unroll
+              for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
+          e = U;
         }
-        int32_t e = e0 + 1;
-        for (; e + 4 <= e1; e += 4) {
-          Pack<T, VB> y[4];
+        for (; e < b.n; e += U) {
+          Pack<T, VB> y[U];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) y[u] = ld<T, VB>(a.leaf, int64_t(a.m_leaf[e + u]) * nv + v);
+          for (int u = 0; u < U; ++u)
+            if (e + u < b.n) y[u] = ld<T, VB>(a.leaf, int64_t(__ldg(lidx + e + u)) * nv + v);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < U; ++u)
+            if (e + u < b.n)
 #pragma unroll
-            for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
+              for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
         }
-        for (; e < e1; ++e) {
-          const Pack<T, VB> y = ld<T, VB>(a.leaf, int64_t(a.m_leaf[e]) * nv + v);
-#pragma unroll
-          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y.v[l]));
-        }
-        const int32_t nch = (mp1 - mp0 + FOLD_BLOCK - 1) / FOLD_BLOCK;
-        bool finish = nch == 1;
+        bool finish = b.comb < 0;
         if (!finish) {
-          const int64_t slot = a.m_slot[m];
-          const int32_t ci = (e0 - mp0) / FOLD_BLOCK;
-          st_cg<A, AVB>(a.partial, (slot + ci) * nv + v, acc);
+          const Comb cb = a.combs[b.comb];
+          const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;
+          st_cg<A, AVB>(a.partial, (int64_t(cb.slot) + ci) * nv + v, acc);
           __threadfence();
-          int32_t *ctr = a.counter + int64_t(a.m_ctr[m]) * nv + v;
-          if (atomicAdd(ctr, 1) == nch - 1) {
+          int32_t *ctr = a.counter + int64_t(cb.ctr) * nv + v;
+          if (atomicAdd(ctr, 1) == cb.nch - 1) {
             __threadfence();
-            acc = fold_partials<A, AVB, OP>(a.partial, slot, nv, v, nch);
+            acc = fold_partials<A, AVB, OP>(a.partial, cb.slot, nv, v, cb.nch);
             *ctr = 0;   // ready for the next operation
             finish = true;
+            xr = ld<T, VB>(a.root, ri);
           }
         }
         if (finish) {
-          Pack<T, VB> x = ld<T, VB>(a.root, ri);
 #pragma unroll
-          for (int l = 0; l < Pack<T, VB>::L; ++l) x.v[l] = apply_acc<OP, T, A>(x.v[l], acc.v[l]);
-          st<T, VB>(a.root, ri, x);
+          for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
+          st<T, VB>(a.root, ri, xr);
         }
       }
     }
   }
+}
+
+template <typename T, int VB, int OP, int MODE>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB>::value)) rm_kernel(RmArgs a) {
+  const RmTile t = a.tiles[blockIdx.x];
+  rm_tile<T, VB, OP, MODE>(a, t);
 }
 
 }  // namespace sfgb

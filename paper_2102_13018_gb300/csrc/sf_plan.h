@@ -15,9 +15,10 @@
 namespace sfgb {
 
 constexpr int FOLD_BLOCK = 64;        // block of the fold D (SF_FOLD_BLOCK)
-constexpr int TS_TILE_EDGES = 2048;   // edges per tile of a TS run
+constexpr int TS_TILE_EDGES = 4096;   // edges per tile of a TS run
 constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile
-constexpr int RM_TILE_CHUNKS = 64;    // fold blocks per chunk tile
+constexpr int RM_TILE_CHUNKS = 1024;  // fold blocks per chunk tile (at most)
+constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most)
 constexpr int RM_TILE_ROOTS = 1024;   // multi roots per winner tile
 constexpr int RM_TILE_FETCH = 128;    // multi roots per fetch tile
 
@@ -53,9 +54,48 @@ enum TileKind : int32_t {
   T_FETCH = 5,     // RM multi roots, serial fetch-and-op
 };
 
+// A slice [k0, k0+cnt) of a TS run with the run's description inlined (one 96-byte load,
+// prefetched by the kernel while it works on the previous tile).
+struct TsTile {
+  int64_t root0, rsy, rsz;
+  int64_t leaf0, lsy, lsz;
+  int64_t idx0, rbuf0, lbuf0;
+  int32_t n, nx, ny, flags;
+  int32_t k0, cnt;
+};
+static_assert(sizeof(TsTile) == 96, "TsTile is copied in 16-byte pieces");
+
+// A tile of the root-major plan; masked tiles carry their run inline.
+struct RmTile {
+  int32_t kind;              // T_MASKED, T_PAIRS, T_CHUNKS, T_WINNERS, T_FETCH
+  int32_t a;                 // first pair / block / multi root
+  int32_t k0;                // masked: first root of the slice inside the run
+  int32_t cnt;               // roots / pairs / blocks in the tile
+  int64_t root0, leaf0;      // masked run start
+  int64_t mask0;             // masked run's first mask bit
+  int64_t pad;
+};
+static_assert(sizeof(RmTile) == 48, "RmTile is copied in 16-byte pieces");
+
 struct MaskedRun {
   int64_t root0, leaf0, mask0;   // mask0: first bit (multiple of 32) in the mask words
   int32_t n, pad;
+};
+
+// One fold block of a multi-leaf root: leaves m_leaf[e0 .. e0+n).
+struct Block {
+  int32_t root;   // root unit
+  int32_t e0;     // first edge of the block in m_leaf
+  int32_t n;      // leaves in the block (1..FOLD_BLOCK)
+  int32_t comb;   // -1 when the root has one block, else its Comb record
+};
+
+// A root with several fold blocks: where its block partials and arrival counter live.
+struct Comb {
+  int32_t slot;     // first partial slot
+  int32_t ctr;      // counter index
+  int32_t nch;      // number of blocks
+  int32_t e_first;  // first edge of the root in m_leaf
 };
 
 struct SegCopy {                 // one (root rank -> leaf rank) chunk of the buffer move
@@ -65,25 +105,22 @@ struct SegCopy {                 // one (root rank -> leaf rank) chunk of the bu
 // Device view of every plan array (pointers into one device allocation).
 struct DevPlan {
   // TS plan
-  const Run *runs;
   const int32_t *ts_ridx, *ts_lidx;
-  const Tile *ts_tiles;          // all runs
-  const Tile *ts_self_tiles;     // self runs only (3-phase: direct scatter)
-  const Tile *ts_remote_tiles;   // remote runs only (3-phase: pack / unpack)
+  const TsTile *ts_tiles;        // all runs
+  const TsTile *ts_self_tiles;   // self runs only (3-phase: direct scatter)
+  const TsTile *ts_remote_tiles; // remote runs only (3-phase: pack / unpack)
   const SegCopy *segs;           // remote segments for the move
   int32_t n_ts_tiles, n_ts_self_tiles, n_ts_remote_tiles, n_segs;
   int64_t remote_units;          // units in each 3-phase buffer
   // RM plan
-  const MaskedRun *mruns;
   const uint32_t *mask;
   const int32_t *pr_root, *pr_leaf;
   const int32_t *m_root, *m_ptr, *m_leaf;   // multi roots: root unit, CSR pointers, leaf units
-  const int32_t *m_slot;                    // first partial slot, -1 for a single-block root
-  const int32_t *m_ctr;                     // counter index, -1 for a single-block root
-  const int32_t *ch_m, *ch_e0;              // fold block -> multi root, first edge
-  const Tile *rm_fold_tiles;                // masked + pairs + chunks
-  const Tile *rm_winner_tiles;              // masked + pairs + winners
-  const Tile *rm_fetch_tiles;               // masked + pairs + fetch
+  const Block *blocks;                      // fold blocks of multi roots
+  const Comb *combs;                        // multi roots with several blocks
+  const RmTile *rm_fold_tiles;              // masked + pairs + chunks
+  const RmTile *rm_winner_tiles;            // masked + pairs + winners
+  const RmTile *rm_fetch_tiles;             // masked + pairs + fetch
   int32_t n_rm_fold_tiles, n_rm_winner_tiles, n_rm_fetch_tiles;
   int32_t n_multi, n_partial_slots, n_counters;
 };

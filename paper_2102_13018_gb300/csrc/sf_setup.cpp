@@ -195,9 +195,23 @@ struct RunBuilder {
   }
 };
 
-void push_tiles(std::vector<Tile> &out, int32_t kind, int32_t a, int64_t n, int64_t per) {
-  for (int64_t k0 = 0; k0 < n; k0 += per)
-    out.push_back(Tile{kind, a, int32_t(k0), int32_t(std::min<int64_t>(per, n - k0))});
+void push_ts_tiles(std::vector<TsTile> &out, const Run &r, int64_t per) {
+  for (int64_t k0 = 0; k0 < r.n; k0 += per) {
+    TsTile t{};
+    t.root0 = r.root0; t.rsy = r.rsy; t.rsz = r.rsz;
+    t.leaf0 = r.leaf0; t.lsy = r.lsy; t.lsz = r.lsz;
+    t.idx0 = r.idx0; t.rbuf0 = r.rbuf0; t.lbuf0 = r.lbuf0;
+    t.n = r.n; t.nx = r.nx; t.ny = r.ny; t.flags = r.flags;
+    t.k0 = int32_t(k0);
+    t.cnt = int32_t(std::min<int64_t>(per, r.n - k0));
+    out.push_back(t);
+  }
+}
+
+RmTile rm_tile(int32_t kind, int32_t a, int32_t k0, int32_t cnt) {
+  RmTile t{};
+  t.kind = kind; t.a = a; t.k0 = k0; t.cnt = cnt;
+  return t;
 }
 
 }  // namespace
@@ -278,9 +292,8 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
     }
     for (size_t r = 0; r < plan.runs.size(); ++r) {
       const Run &run = plan.runs[r];
-      push_tiles(plan.ts_tiles, T_RUN, int32_t(r), run.n, TS_TILE_EDGES);
-      push_tiles((run.flags & RUN_SELF) ? plan.ts_self_tiles : plan.ts_remote_tiles, T_RUN, int32_t(r), run.n,
-                 TS_TILE_EDGES);
+      push_ts_tiles(plan.ts_tiles, run, TS_TILE_EDGES);
+      push_ts_tiles((run.flags & RUN_SELF) ? plan.ts_self_tiles : plan.ts_remote_tiles, run, TS_TILE_EDGES);
       info.runs++;
       const int32_t idx = run.flags & (RUN_ROOT_IDX | RUN_LEAF_IDX);
       if (idx == 0) {
@@ -358,36 +371,42 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       close();
     }
     // fold blocks of multi roots
-    plan.m_slot.assign(M, -1);
-    plan.m_ctr.assign(M, -1);
+    std::vector<int32_t> blk_m;   // block -> multi root (host only, for tiling)
     std::vector<uint8_t> heavy(M, 0);
     for (int32_t m = 0; m < M; ++m) {
       const int32_t d = plan.m_ptr[m + 1] - plan.m_ptr[m];
       const int32_t nch = (d + FOLD_BLOCK - 1) / FOLD_BLOCK;
-      for (int32_t c = 0; c < nch; ++c) {
-        plan.ch_m.push_back(m);
-        plan.ch_e0.push_back(plan.m_ptr[m] + c * FOLD_BLOCK);
-      }
+      int32_t comb = -1;
       if (nch > 1) {
-        plan.m_slot[m] = plan.n_partial_slots;
+        comb = int32_t(plan.combs.size());
+        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_counters, nch, plan.m_ptr[m]});
         plan.n_partial_slots += nch;
-        plan.m_ctr[m] = plan.n_counters++;
+        plan.n_counters++;
+      }
+      for (int32_t c = 0; c < nch; ++c) {
+        const int32_t e0 = plan.m_ptr[m] + c * FOLD_BLOCK;
+        plan.blocks.push_back(Block{plan.m_root[m], e0, std::min(FOLD_BLOCK, plan.m_ptr[m + 1] - e0), comb});
+        blk_m.push_back(m);
       }
       heavy[m] = nch >= 16;
     }
     // tiles, ordered by the first root they touch (heavy multi roots first)
-    struct Keyed { int64_t key; Tile t; };
+    struct Keyed { int64_t key; RmTile t; };
     std::vector<Keyed> common;
     for (size_t i = 0; i < plan.mruns.size(); ++i)
-      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += RM_TILE_EDGES)
-        common.push_back({plan.mruns[i].root0 + k0,
-                          Tile{T_MASKED, int32_t(i), int32_t(k0),
-                               int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.mruns[i].n - k0))}});
+      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += RM_TILE_EDGES) {
+        RmTile t = rm_tile(T_MASKED, int32_t(i), int32_t(k0),
+                           int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.mruns[i].n - k0)));
+        t.root0 = plan.mruns[i].root0;
+        t.leaf0 = plan.mruns[i].leaf0;
+        t.mask0 = plan.mruns[i].mask0;
+        common.push_back({plan.mruns[i].root0 + k0, t});
+      }
     for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += RM_TILE_EDGES)
-      common.push_back({plan.pr_root[i], Tile{T_PAIRS, int32_t(i), 0,
-                                              int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.pr_root.size() - i))}});
+      common.push_back({plan.pr_root[i], rm_tile(T_PAIRS, int32_t(i), 0,
+                                                 int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.pr_root.size() - i)))});
     const int64_t heavy_key = -(int64_t(1) << 40);
-    auto finish = [&](std::vector<Keyed> extra, std::vector<Tile> &out) {
+    auto finish = [&](std::vector<Keyed> extra, std::vector<RmTile> &out) {
       extra.insert(extra.end(), common.begin(), common.end());
       std::stable_sort(extra.begin(), extra.end(), [](const Keyed &a, const Keyed &b) { return a.key < b.key; });
       out.clear();
@@ -395,18 +414,19 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
     };
     {
       std::vector<Keyed> ch;
-      const int64_t nchunks = int64_t(plan.ch_m.size());
+      const int64_t nblocks = int64_t(plan.blocks.size());
       int64_t c = 0;
-      while (c < nchunks) {
-        const int32_t m = plan.ch_m[c];
-        int64_t c1 = c;
-        if (heavy[m]) {   // a heavy root's blocks get tiles of their own
-          while (c1 < nchunks && plan.ch_m[c1] == m && c1 - c < RM_TILE_CHUNKS) ++c1;
+      while (c < nblocks) {
+        const int32_t m = blk_m[c];
+        int64_t c1 = c, edges = 0;
+        if (heavy[m]) {   // a heavy root's blocks get tiles of their own, scheduled first
+          while (c1 < nblocks && blk_m[c1] == m && c1 - c < RM_TILE_CHUNKS / 4) edges += plan.blocks[c1++].n;
         } else {
-          while (c1 < nchunks && !heavy[plan.ch_m[c1]] && c1 - c < RM_TILE_CHUNKS) ++c1;
+          while (c1 < nblocks && !heavy[blk_m[c1]] && c1 - c < RM_TILE_CHUNKS && edges < RM_TILE_CHUNK_EDGES)
+            edges += plan.blocks[c1++].n;
         }
         ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]),
-                      Tile{T_CHUNKS, int32_t(c), 0, int32_t(c1 - c)}});
+                      rm_tile(T_CHUNKS, int32_t(c), 0, int32_t(c1 - c))});
         c = c1;
       }
       finish(ch, plan.rm_fold_tiles);
@@ -414,7 +434,7 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
     {
       std::vector<Keyed> w;
       for (int32_t m = 0; m < M; m += RM_TILE_ROOTS)
-        w.push_back({plan.m_root[m], Tile{T_WINNERS, m, 0, std::min<int32_t>(RM_TILE_ROOTS, M - m)}});
+        w.push_back({plan.m_root[m], rm_tile(T_WINNERS, m, 0, std::min<int32_t>(RM_TILE_ROOTS, M - m))});
       finish(w, plan.rm_winner_tiles);
     }
     {
@@ -427,7 +447,7 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
           edges += plan.m_ptr[m1 + 1] - plan.m_ptr[m1];
           ++m1;
         }
-        f.push_back({plan.m_root[m], Tile{T_FETCH, m, 0, m1 - m}});
+        f.push_back({plan.m_root[m], rm_tile(T_FETCH, m, 0, m1 - m)});
         m = m1;
       }
       finish(f, plan.rm_fetch_tiles);
@@ -450,7 +470,7 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       for (int32_t k = 0; k < mr.n; ++k)
         info.rm_masked_edges += (plan.mask[(mr.mask0 + k) >> 5] >> ((mr.mask0 + k) & 31)) & 1u;
     info.rm_pairs = int64_t(plan.pr_root.size());
-    info.rm_chunks = int64_t(plan.ch_m.size());
+    info.rm_chunks = int64_t(plan.blocks.size());
     info.analyzed = 1;
   } catch (const std::bad_alloc &) {
     return SF_ERR_ALLOC;
