@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -302,6 +303,35 @@ def main():
            "reduce_frac": rb / (r_avg * 1e-3) / 1e9 / peak, "bcast_bytes": bb, "reduce_bytes": rb,
            "setup_s": setup_s, "host_wall_s": wall}
 
+    # the other data paths on the same forest, timed the same way (not part of the step)
+    variants = {}
+    if not args.no_variants:
+        def time_op(fn, reps=30):
+            ts = []
+            for i in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= 3:
+                    ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+        for path in ("fused", "three_phase", "root_major"):
+            sf.set_path(path)
+            ms = time_op(lambda: sf.bcast(x, lvec, "REPLACE", stream=stream))
+            variants[f"bcast_{path}"] = {"ms": ms, "gbs": bb / (ms * 1e-3) / 1e9}
+        sf.set_path("fused")
+        for mode in ("deterministic", "atomic"):
+            sf.set_mode(mode)
+            ms = time_op(lambda: sf.reduce(lvec, y, "SUM", stream=stream))
+            variants[f"reduce_sum_{mode}"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
+        sf.set_mode("deterministic")
+        ms = time_op(lambda: sf._lib.sf_reduce_noalloc(sf._h, sf._unit(y, sf.nroots_total, None),
+                                                      sf._ptr(lvec), sf._ptr(y), 1, sf._stream(stream)))
+        variants["reduce_sum_noalloc"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
+
     # end to end through the public API with pinned host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -344,7 +374,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "ops": ops,
+                "clocks": clk, "ops": ops, "variants": variants,
                 "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
                                               "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
                                               "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}

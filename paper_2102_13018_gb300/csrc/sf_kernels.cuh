@@ -292,39 +292,51 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &r) {
       }
       return;
     }
-    if (d_flat && s_idx) {
-      // gather: destination contiguous, source through the index array
-      const int32_t *sidx = (L2R ? a.lidx : a.ridx) + r.idx0 + t.k0;
-      const int64_t db = (d0 + t.k0) * nv;
-      const int32_t nvec = t.cnt * nv;
-      constexpr int UG = VB >= 16 ? 4 : 8;
-      for (int32_t base = threadIdx.x; base < nvec; base += kThreads * UG) {
-        int64_t su[UG];
-        Pack<T, VB> x[UG];
+  }
+  if ((s_flat || s_idx) && (d_flat || d_idx)) {
+    // each side contiguous or indexed: gathers, scatters, both indexed, atomics
+    const int32_t *sidx = (L2R ? a.lidx : a.ridx) + t.idx0 + t.k0;
+    const int32_t *didx = (L2R ? a.ridx : a.lidx) + t.idx0 + t.k0;
+    const int64_t sb = s0 + t.k0, db = d0 + t.k0;
+    const int32_t nvec = t.cnt * nv;
+    constexpr int UG = VB >= 16 ? 2 : 4;
+    for (int32_t base = threadIdx.x; base < nvec; base += kThreads * UG) {
+      int64_t si[UG], di[UG];
 #pragma unroll
-        for (int u = 0; u < UG; ++u) {
-          const int32_t w = base + u * kThreads;
-          const int32_t k = nv == 1 ? w : w / nv;
-          su[u] = w < nvec ? int64_t(__ldg(sidx + k)) * nv + (w - k * nv) : 0;
-        }
+      for (int u = 0; u < UG; ++u) {
+        const int32_t w = base + u * kThreads;
+        const int32_t k = w < nvec ? (nv == 1 ? w : w / nv) : 0;
+        const int32_t v = w < nvec ? w - k * nv : 0;
+        si[u] = (s_idx ? int64_t(__ldg(sidx + k)) : sb + k) * nv + v;
+        di[u] = (d_idx ? int64_t(__ldg(didx + k)) : db + k) * nv + v;
+      }
+      Pack<T, VB> x[UG];
+#pragma unroll
+      for (int u = 0; u < UG; ++u)
+        if (base + u * kThreads < nvec) x[u] = ld<T, VB>(a.src, si[u]);
+      if constexpr (ATOMIC) {
+        static_assert(VB == sizeof(T), "atomics are element-wise");
 #pragma unroll
         for (int u = 0; u < UG; ++u)
-          if (base + u * kThreads < nvec) x[u] = ld<T, VB>(a.src, su[u]);
-        if constexpr (OP == OP_REPLACE) {
+          if (base + u * kThreads < nvec) {
+            const T old = atomic_apply<OP>(reinterpret_cast<T *>(a.dst) + di[u], x[u].v[0]);
+            if constexpr (FETCH) reinterpret_cast<T *>(a.upd)[si[u]] = old;   // source side = leaf
+          }
+      } else if constexpr (OP == OP_REPLACE) {
 #pragma unroll
-          for (int u = 0; u < UG; ++u)
-            if (base + u * kThreads < nvec) st<T, VB>(a.dst, db + base + u * kThreads, x[u]);
-        } else {
+        for (int u = 0; u < UG; ++u)
+          if (base + u * kThreads < nvec) st<T, VB>(a.dst, di[u], x[u]);
+      } else {
+        Pack<T, VB> y[UG];
 #pragma unroll
-          for (int u = 0; u < UG; ++u)
-            if (base + u * kThreads < nvec) {
-              const int64_t di = db + base + u * kThreads;
-              st<T, VB>(a.dst, di, combine<OP, T, VB>(ld<T, VB>(a.dst, di), x[u]));
-            }
-        }
+        for (int u = 0; u < UG; ++u)
+          if (base + u * kThreads < nvec) y[u] = ld<T, VB>(a.dst, di[u]);
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          if (base + u * kThreads < nvec) st<T, VB>(a.dst, di[u], combine<OP, T, VB>(y[u], x[u]));
       }
-      return;
     }
+    return;
   }
   // general: pattern or index on either side
   const int64_t work = int64_t(t.cnt) * nv;
@@ -381,14 +393,14 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &r) {
 
 // Resident CTAs per SM the register budget must allow: copies are lean, op kernels carry
 // arithmetic and more live state.
-template <int OP, int VB> struct MinBlocks {
-  static constexpr int value = OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 4);
+template <int OP, int VB, bool ATOMIC = false> struct MinBlocks {
+  static constexpr int value = ATOMIC ? 4 : OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 3);
 };
 
 // One CTA per tile (the hardware balances uneven tiles); the tile carries its run inline so a
 // single descriptor load precedes the data.
 template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
-__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB>::value)) ts_kernel(TsArgs a) {
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, ATOMIC>::value)) ts_kernel(TsArgs a) {
   const TsTile t = a.tiles[blockIdx.x];
   ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
 }
@@ -486,6 +498,136 @@ template <int OP, int MODE> struct SingleReads {
   static constexpr bool leaf = !(MODE == RM_BCAST && OP == OP_REPLACE);
 };
 
+// One fold block of a multi-leaf root, vector v: Bcast writes the root to the block's leaves;
+// Reduce folds the block's leaves in canonical order and either applies the result to the
+// root (single-block root) or leaves a partial whose last arriver folds all partials by D.
+template <typename T, int VB, int OP, int MODE>
+__device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t *m_leaf, const Comb *combs,
+                                           void *partial, int32_t *counter, int32_t nv, const Block b, int32_t v) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  constexpr int U = VB >= 16 ? 2 : 4;
+  const int64_t ri = int64_t(b.root) * nv + v;
+  const int32_t *lidx = m_leaf + b.e0;
+  if constexpr (MODE == RM_BCAST) {
+    const Pack<T, VB> x = ld<T, VB>(root, ri);
+    for (int32_t e = 0; e < b.n; e += U) {
+      int64_t li[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) li[u] = e + u < b.n ? int64_t(__ldg(lidx + e + u)) * nv + v : 0;
+      if constexpr (OP == OP_REPLACE) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e + u < b.n) st<T, VB>(leaf, li[u], x);
+      } else {
+        Pack<T, VB> y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e + u < b.n) y[u] = ld<T, VB>(leaf, li[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e + u < b.n) st<T, VB>(leaf, li[u], combine<OP, T, VB>(y[u], x));
+      }
+    }
+  } else if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
+    // left fold of this block in canonical order, U leaves in flight
+    Pack<T, VB> xr;
+    if (b.comb < 0) xr = ld<T, VB>(root, ri);   // issued early: independent of the fold
+    Pack<A, AVB> acc;
+    int32_t e = 0;
+    {
+      Pack<T, VB> y[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u < b.n) y[u] = ld<T, VB>(leaf, int64_t(__ldg(lidx + u)) * nv + v);
+#pragma unroll
+      for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = to_acc<A, T>(y[0].v[l]);
+#pragma unroll
+      for (int u = 1; u < U; ++u)
+        if (u < b.n)
+#pragma unroll
+          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
+      e = U;
+    }
+    for (; e < b.n; e += U) {
+      Pack<T, VB> y[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e + u < b.n) y[u] = ld<T, VB>(leaf, int64_t(__ldg(lidx + e + u)) * nv + v);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e + u < b.n)
+#pragma unroll
+          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
+    }
+    bool finish = b.comb < 0;
+    if (!finish) {
+      const Comb cb = combs[b.comb];
+      const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;
+      st_cg<A, AVB>(partial, (int64_t(cb.slot) + ci) * nv + v, acc);
+      __threadfence();
+      int32_t *ctr = counter + int64_t(cb.ctr) * nv + v;
+      if (atomicAdd(ctr, 1) == cb.nch - 1) {
+        __threadfence();
+        acc = fold_partials<A, AVB, OP>(partial, cb.slot, nv, v, cb.nch);
+        *ctr = 0;   // ready for the next operation
+        finish = true;
+        xr = ld<T, VB>(root, ri);
+      }
+    }
+    if (finish) {
+#pragma unroll
+      for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
+      st<T, VB>(root, ri, xr);
+    }
+  }
+}
+
+// Two single-block roots folded together (Reduce SUM/MIN/MAX): both descriptors, then U + U
+// leaf indices, then U + U leaf values are in flight at once, so each thread keeps two
+// independent load chains going.
+template <typename T, int VB, int OP>
+__device__ __forceinline__ void fold_pair(void *root, void *leaf, const int32_t *m_leaf, int32_t nv, const Block b0,
+                                          const Block b1, int32_t v0, int32_t v1) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  constexpr int U = VB >= 16 ? 1 : 2;
+  const int64_t ri0 = int64_t(b0.root) * nv + v0, ri1 = int64_t(b1.root) * nv + v1;
+  const Pack<T, VB> x0 = ld<T, VB>(root, ri0), x1 = ld<T, VB>(root, ri1);
+  Pack<A, AVB> acc0, acc1;
+  const int32_t nmax = b0.n > b1.n ? b0.n : b1.n;
+  for (int32_t e = 0; e < nmax; e += U) {
+    int64_t l0[U], l1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      l0[u] = e + u < b0.n ? int64_t(__ldg(m_leaf + b0.e0 + e + u)) * nv + v0 : -1;
+      l1[u] = e + u < b1.n ? int64_t(__ldg(m_leaf + b1.e0 + e + u)) * nv + v1 : -1;
+    }
+    Pack<T, VB> y0[U], y1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (l0[u] >= 0) y0[u] = ld<T, VB>(leaf, l0[u]);
+      if (l1[u] >= 0) y1[u] = ld<T, VB>(leaf, l1[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int l = 0; l < Pack<T, VB>::L; ++l) {
+        if (l0[u] >= 0) acc0.v[l] = (e + u == 0) ? to_acc<A, T>(y0[u].v[l]) : combine<OP, A>(acc0.v[l], to_acc<A, T>(y0[u].v[l]));
+        if (l1[u] >= 0) acc1.v[l] = (e + u == 0) ? to_acc<A, T>(y1[u].v[l]) : combine<OP, A>(acc1.v[l], to_acc<A, T>(y1[u].v[l]));
+      }
+    }
+  }
+  Pack<T, VB> r0 = x0, r1 = x1;
+#pragma unroll
+  for (int l = 0; l < Pack<T, VB>::L; ++l) {
+    r0.v[l] = apply_acc<OP, T, A>(x0.v[l], acc0.v[l]);
+    r1.v[l] = apply_acc<OP, T, A>(x1.v[l], acc1.v[l]);
+  }
+  st<T, VB>(root, ri0, r0);
+  st<T, VB>(root, ri1, r1);
+}
+
 template <typename T, int VB, int OP, int MODE>
 __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   using A = typename Acc<T, OP>::type;
@@ -493,7 +635,46 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   constexpr int U = VB >= 16 ? 2 : 4;
   const int32_t nv = a.nv;
   const int32_t work = t.cnt * nv;
-  if (t.kind == T_MASKED || t.kind == T_PAIRS) {
+  if (t.kind == T_MASKED && nv == 1) {
+    // Scalar units: root, leaf and mask word of an edge are independent loads (every unit in
+    // the run's span is valid memory; only the store waits for the mask bit), 8 edges in
+    // flight per thread, 32-bit offsets from the tile's base pointers.
+    constexpr int UM = VB >= 16 ? 4 : 8;
+    constexpr bool need_root = SingleReads<OP, MODE>::root, need_leaf = SingleReads<OP, MODE>::leaf;
+    T *rbase = static_cast<T *>(a.root) + (t.root0 + t.k0) * Pack<T, VB>::L;
+    T *lbase = static_cast<T *>(a.leaf) + (t.leaf0 + t.k0) * Pack<T, VB>::L;
+    T *ubase = MODE == RM_FETCH ? static_cast<T *>(a.upd) + (t.leaf0 + t.k0) * Pack<T, VB>::L : nullptr;
+    const uint32_t *mw = a.mask + ((t.mask0 + t.k0) >> 5);   // mask0 and k0 are multiples of 32
+    for (int32_t base = threadIdx.x; base < t.cnt; base += kThreads * UM) {
+      uint32_t mk[UM];
+      Pack<T, VB> x[UM], y[UM];
+#pragma unroll
+      for (int u = 0; u < UM; ++u) {
+        const int32_t k = base + u * kThreads;
+        mk[u] = 0;
+        if (k < t.cnt) {
+          mk[u] = (__ldg(mw + (k >> 5)) >> (k & 31)) & 1u;
+          if constexpr (need_root) x[u] = ld<T, VB>(rbase, k);
+          if constexpr (need_leaf) y[u] = ld<T, VB>(lbase, k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UM; ++u) {
+        const int32_t k = base + u * kThreads;
+        if (!mk[u]) continue;
+        if constexpr (MODE == RM_BCAST) {
+          if constexpr (OP == OP_REPLACE) st<T, VB>(lbase, k, x[u]);
+          else st<T, VB>(lbase, k, combine<OP, T, VB>(y[u], x[u]));
+        } else if constexpr (MODE == RM_REDUCE) {
+          if constexpr (OP == OP_REPLACE) st<T, VB>(rbase, k, y[u]);
+          else st<T, VB>(rbase, k, combine<OP, T, VB>(x[u], y[u]));
+        } else {
+          st<T, VB>(ubase, k, x[u]);
+          st<T, VB>(rbase, k, combine<OP, T, VB>(x[u], y[u]));
+        }
+      }
+    }
+  } else if (t.kind == T_MASKED || t.kind == T_PAIRS) {
     const RmTile &mr = t;
     for (int32_t base = threadIdx.x; base < work; base += kThreads * U) {
       int64_t ri[U], li[U];
@@ -554,89 +735,31 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       }
     }
   } else if (t.kind == T_CHUNKS) {
-    for (int32_t w = threadIdx.x; w < work; w += kThreads) {
-      const int32_t cl = nv == 1 ? w : w / nv, v = w - cl * nv;
-      const Block b = a.blocks[t.a + cl];
-      const int64_t ri = int64_t(b.root) * nv + v;
-      const int32_t *lidx = a.m_leaf + b.e0;
-      if constexpr (MODE == RM_BCAST) {
-        const Pack<T, VB> x = ld<T, VB>(a.root, ri);
-        for (int32_t e = 0; e < b.n; e += U) {
-          int64_t li[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) li[u] = e + u < b.n ? int64_t(__ldg(lidx + e + u)) * nv + v : 0;
-          if constexpr (OP == OP_REPLACE) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (e + u < b.n) st<T, VB>(a.leaf, li[u], x);
-          } else {
-            Pack<T, VB> y[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (e + u < b.n) y[u] = ld<T, VB>(a.leaf, li[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-              if (e + u < b.n) st<T, VB>(a.leaf, li[u], combine<OP, T, VB>(y[u], x));
-          }
-        }
-      } else if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
-        // left fold of this block in canonical order, U leaves in flight
-        Pack<T, VB> xr;
-        if (b.comb < 0) xr = ld<T, VB>(a.root, ri);   // issued early: independent of the fold
-        Pack<A, AVB> acc;
-        int32_t e = 0;
-        {
-          Pack<T, VB> y[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (u < b.n) y[u] = ld<T, VB>(a.leaf, int64_t(__ldg(lidx + u)) * nv + v);
-#pragma unroll
-          for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = to_acc<A, T>(y[0].v[l]);
-#pragma unroll
-          for (int u = 1; u < U; ++u)
-            if (u < b.n)
-#pragma unroll
-              for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
-          e = U;
-        }
-        for (; e < b.n; e += U) {
-          Pack<T, VB> y[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (e + u < b.n) y[u] = ld<T, VB>(a.leaf, int64_t(__ldg(lidx + e + u)) * nv + v);
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (e + u < b.n)
-#pragma unroll
-              for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
-        }
-        bool finish = b.comb < 0;
-        if (!finish) {
-          const Comb cb = a.combs[b.comb];
-          const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;
-          st_cg<A, AVB>(a.partial, (int64_t(cb.slot) + ci) * nv + v, acc);
-          __threadfence();
-          int32_t *ctr = a.counter + int64_t(cb.ctr) * nv + v;
-          if (atomicAdd(ctr, 1) == cb.nch - 1) {
-            __threadfence();
-            acc = fold_partials<A, AVB, OP>(a.partial, cb.slot, nv, v, cb.nch);
-            *ctr = 0;   // ready for the next operation
-            finish = true;
-            xr = ld<T, VB>(a.root, ri);
-          }
-        }
-        if (finish) {
-#pragma unroll
-          for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
-          st<T, VB>(a.root, ri, xr);
+    int32_t w = threadIdx.x;
+    if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
+      // pairs of work items: w and w + kThreads
+      for (; w + kThreads < work; w += 2 * kThreads) {
+        const int32_t c0 = nv == 1 ? w : w / nv, v0 = w - c0 * nv;
+        const int32_t w1 = w + kThreads, c1 = nv == 1 ? w1 : w1 / nv, v1 = w1 - c1 * nv;
+        const Block b0 = a.blocks[t.a + c0], b1 = a.blocks[t.a + c1];
+        if (b0.comb < 0 && b1.comb < 0) {
+          fold_pair<T, VB, OP>(a.root, a.leaf, a.m_leaf, nv, b0, b1, v0, v1);
+        } else {
+          fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b0, v0);
+          fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b1, v1);
         }
       }
+    }
+    for (; w < work; w += kThreads) {
+      const int32_t cl = nv == 1 ? w : w / nv, v = w - cl * nv;
+      fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv,
+                                  a.blocks[t.a + cl], v);
     }
   }
 }
 
 template <typename T, int VB, int OP, int MODE>
-__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB>::value)) rm_kernel(RmArgs a) {
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>::value)) rm_kernel(RmArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
   rm_tile<T, VB, OP, MODE>(a, t);
 }

@@ -16,6 +16,7 @@ cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fet
 cudaError_t launch_move(int vb, const MoveArgs &a, int ntiles, cudaStream_t s);
 cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
 
+
 // per-dtype instantiations (one translation unit each)
 template <typename T> cudaError_t launch_rm_t(int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
 template <typename T>

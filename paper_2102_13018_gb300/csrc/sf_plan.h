@@ -54,6 +54,7 @@ enum TileKind : int32_t {
   T_FETCH = 5,     // RM multi roots, serial fetch-and-op
 };
 
+
 // A slice [k0, k0+cnt) of a TS run with the run's description inlined (one 96-byte load,
 // prefetched by the kernel while it works on the previous tile).
 struct TsTile {
