@@ -196,6 +196,46 @@ int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, cons
 int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
                                int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
 
+/* ---- Batched execution (Sec. V.D: launch cost and pipelining; CUDA graphs as future work) ----
+ * A batch runs many forests' operations with few kernel launches: operations are grouped by
+ * kernel variant (element type, op, vector width, data path, Reduce mode) and each group is one
+ * launch over all of its operations' tiles.  SF_OP_BARRIER entries split the list into stages
+ * that run in order; operations inside a stage run in no particular order and must not write
+ * memory that another operation of the same stage reads or writes (and a forest may appear in
+ * only one Reduce of a stage).  Each operation uses its forest's current path and mode; the
+ * three-phase path runs as the fused path inside a batch. */
+enum { SF_OP_BCAST = 0, SF_OP_REDUCE = 1, SF_OP_BARRIER = 2 };
+
+typedef struct {
+  sf_t *sf;        /* a set-up forest (ignored for SF_OP_BARRIER) */
+  int32_t kind;    /* SF_OP_BCAST, SF_OP_REDUCE or SF_OP_BARRIER */
+  sf_unit unit;
+  int32_t op;      /* SF_REPLACE .. SF_MAX */
+  const void *src; /* Bcast: rootdata; Reduce: leafdata (device memory) */
+  void *dst;       /* Bcast: leafdata; Reduce: rootdata (device memory) */
+} sf_batch_op;
+
+int sf_batch_create(sf_batch_t **out);
+
+/* Run ops[0..n) on `stream`.  The first call with a given list (or after a forest's path or
+ * mode changed) builds and uploads the batch's tables, which allocates device memory and
+ * synchronises `stream`; later calls with the same list only launch.  With use_graph != 0 the
+ * launches are captured once into a CUDA graph (on a private stream) and every call replays it
+ * with one cudaGraphLaunch on `stream`.  Errors: those of the single operations. */
+int sf_batch_run(sf_batch_t *batch, const sf_batch_op ops[], int32_t n, int32_t use_graph, sf_stream_t stream);
+
+/* Kernel launches one run of the current list takes (its number of variant groups). */
+int sf_batch_launches(const sf_batch_t *batch, int32_t *launches);
+int sf_batch_destroy(sf_batch_t *batch);
+
+/* Autotuner: times each data path of Bcast (kind SF_OP_BCAST) or each Reduce mode (kind
+ * SF_OP_REDUCE) on this forest, unit and op, `reps` times after one warm-up, writing into a
+ * scratch copy of dst (src and dst are not modified), and makes the fastest the meaning of
+ * SF_PATH_AUTO / SF_MODE_AUTO for the forest.  *choice (may be NULL) receives it.  Allocates
+ * and synchronises `stream`.  Choosing SF_MODE_ATOMIC trades bit-reproducibility for speed. */
+int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst, int32_t op, int32_t reps,
+                sf_stream_t stream, int32_t *choice);
+
 /* Maximum scratch, in bytes, that sf_reduce_noalloc may use (a fixed device array). */
 #define SF_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -9,6 +9,6 @@ from ._abi import SFError, SF_FOLD_BLOCK
 
 _abi.load()
 
-from .sf import StarForest, launch_count, OPS, MODES, PATHS  # noqa: E402
+from .sf import StarForest, Batch, launch_count, OPS, MODES, PATHS  # noqa: E402
 
-__all__ = ["StarForest", "SFError", "launch_count", "OPS", "MODES", "PATHS", "SF_FOLD_BLOCK"]
+__all__ = ["StarForest", "Batch", "SFError", "launch_count", "OPS", "MODES", "PATHS", "SF_FOLD_BLOCK"]

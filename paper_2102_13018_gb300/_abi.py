@@ -14,6 +14,7 @@ SF_REPLACE, SF_SUM, SF_MIN, SF_MAX = range(4)
 SF_MODE_AUTO, SF_MODE_ATOMIC, SF_MODE_DETERMINISTIC = range(3)
 SF_PATH_AUTO, SF_PATH_FUSED, SF_PATH_THREE_PHASE, SF_PATH_ROOT_MAJOR = range(4)
 SF_MEM_HOST, SF_MEM_DEVICE = 0, 1
+SF_OP_BCAST, SF_OP_REDUCE, SF_OP_BARRIER = 0, 1, 2
 SF_FOLD_BLOCK = 64
 SF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -37,6 +38,11 @@ class sf_node(ctypes.Structure):
 
 class sf_unit(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("bs", ctypes.c_int32)]
+
+
+class sf_batch_op(ctypes.Structure):
+    _fields_ = [("sf", ctypes.c_void_p), ("kind", ctypes.c_int32), ("unit", sf_unit), ("op", ctypes.c_int32),
+                ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p)]
 
 
 class sf_info(ctypes.Structure):
@@ -88,6 +94,11 @@ def load():
                  "sf_reduce_with_memtype_begin", "sf_reduce_with_memtype_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, i32, vp, i32, vp, i32, vp]
     lib.sf_reduce_noalloc.argtypes = [vp, sf_unit, vp, vp, i32, vp]
+    lib.sf_batch_create.argtypes = [P(vp)]
+    lib.sf_batch_run.argtypes = [vp, P(sf_batch_op), i32, i32, vp]
+    lib.sf_batch_launches.argtypes = [vp, P(i32)]
+    lib.sf_batch_destroy.argtypes = [vp]
+    lib.sf_autotune.argtypes = [vp, sf_unit, i32, vp, vp, i32, i32, vp, P(i32)]
     lib.sf_destroy.argtypes = [vp]
     lib.sf_error_string.argtypes = [ctypes.c_int]
     lib.sf_error_string.restype = ctypes.c_char_p

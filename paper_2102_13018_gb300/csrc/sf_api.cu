@@ -9,62 +9,16 @@
 #include <new>
 #include <vector>
 
-#include "sf.h"
-#include "sf_host.h"
-#include "sf_launch.h"
+#include "sf_object.h"
 
 using namespace sfgb;
 
-namespace {
+namespace sfgb {
 
-std::atomic<int64_t> g_launches{0};
-
-enum { K_BCAST = 1, K_REDUCE = 2, K_FETCH = 3, K_BCAST_MT = 4, K_REDUCE_MT = 5 };
-
-struct Pending {
-  int kind;
-  sf_unit unit;
-  const void *p0, *p1, *p2;
-  int32_t op;
-  int32_t m0, m1;      // memtypes (memtype calls)
-  int32_t finish;      // work left for End: 0 none, 1 three-phase unpack
-};
-
-int elem_size(int dtype) {
-  switch (dtype) {
-    case SF_INT32: case SF_FP32: return 4;
-    case SF_INT64: case SF_FP64: return 8;
-    case SF_BF16: return 2;
-  }
-  return 0;
+std::atomic<int64_t> &launch_counter() {
+  static std::atomic<int64_t> count{0};
+  return count;
 }
-
-struct DevBuf {
-  void *p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-struct sf_s {
-  Graph g;
-  HostPlan hp;
-  sf_info info{};
-  bool setup = false;
-  int device = -1;
-  DevBuf blob;                 // all plan arrays
-  DevPlan dp{};
-  std::vector<Tile> h_move_tiles;
-  const Tile *move_tiles = nullptr;
-  int32_t n_move_tiles = 0;
-  DevBuf partial, counter;     // fold scratch
-  DevBuf rootbuf, leafbuf;     // three-phase buffers
-  DevBuf stage_root, stage_leaf;   // memtype staging
-  int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
-  std::vector<Pending> pending;
-};
-
-namespace {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? SF_SUCCESS : SF_ERR_CUDA; }
 
@@ -142,7 +96,7 @@ void drop_pending(sf_t *sf, Pending *pd) { sf->pending.erase(sf->pending.begin()
 
 int launched(cudaError_t e) {
   if (e != cudaSuccess) return SF_ERR_CUDA;
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  launch_counter().fetch_add(1, std::memory_order_relaxed);
   return SF_SUCCESS;
 }
 
@@ -237,7 +191,7 @@ int bcast_finish(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
 int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s) {
   const int w = elem_size(u.dtype), ub = w * u.bs;
   if (sf->info.nedges == 0) return SF_SUCCESS;
-  const bool atomic = sf->mode == SF_MODE_ATOMIC && op != SF_REPLACE && u.dtype != SF_BF16;
+  const bool atomic = reduce_mode(sf) == SF_MODE_ATOMIC && op != SF_REPLACE && u.dtype != SF_BF16;
   if (atomic) {
     TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
     return launched(launch_ts(u.dtype, op, w, true, true, false, a, sf->dp.n_ts_tiles, s));
@@ -274,7 +228,8 @@ int fetch_launch(sf_t *sf, const sf_unit &u, void *root, const void *leaf, void 
   return launched(launch_rm(u.dtype, op, vbo, RM_FETCH, a, sf->dp.n_rm_fetch_tiles, s));
 }
 
-int bcast_path(const sf_t *sf) { return sf->path == SF_PATH_AUTO ? SF_PATH_FUSED : sf->path; }
+int bcast_path(const sf_t *sf) { return sf->path == SF_PATH_AUTO ? sf->tuned_path : sf->path; }
+int reduce_mode(const sf_t *sf) { return sf->mode == SF_MODE_AUTO ? sf->tuned_mode : sf->mode; }
 
 int ensure_ready(const sf_t *sf) {
   if (!sf) return SF_ERR_NULL;
@@ -282,7 +237,22 @@ int ensure_ready(const sf_t *sf) {
   return SF_SUCCESS;
 }
 
-}  // namespace
+int bcast_all(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s, int path) {
+  int finish = 0;
+  int rc = bcast_launch(sf, u, root, leaf, op, s, path, &finish);
+  if (!rc && finish) rc = bcast_finish(sf, u, root, leaf, op, s);
+  return rc;
+}
+
+int reduce_all(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int mode) {
+  const int32_t saved = sf->mode;
+  sf->mode = mode;
+  const int rc = reduce_launch(sf, u, leaf, root, op, s);
+  sf->mode = saved;
+  return rc;
+}
+
+}  // namespace sfgb
 
 extern "C" {
 
@@ -612,7 +582,7 @@ const char *sf_error_string(int code) {
   return "unknown error code";
 }
 
-int64_t sf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+int64_t sf_launch_count(void) { return launch_counter().load(std::memory_order_relaxed); }
 
 }  // extern "C"
 

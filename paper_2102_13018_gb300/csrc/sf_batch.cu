@@ -1,0 +1,335 @@
+// sf_batch.cu -- many forests' operations in few launches, optionally replayed as one CUDA
+// graph, and the per-forest autotuner that picks the data path and Reduce mode.
+//
+// The paper counts about 10 us per kernel launch and shows how host synchronisation breaks the
+// pipelining of launches (Sec. V.D, Fig. "pipelined vs interrupted launches"); its conclusion
+// names CUDA graphs as future work.  A batch therefore groups its operations by kernel variant
+// (element type, op, vector width, path) and launches each group once over a combined tile
+// table of (operation, tile) pairs; with use_graph the launches of a run are captured once and
+// replayed with a single cudaGraphLaunch.
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "sf_object.h"
+
+using namespace sfgb;
+
+namespace {
+
+struct Group {
+  int stage;
+  int family;   // 0 two-sided kernel, 1 root-major kernel
+  int dtype, op, vb, mode;
+  bool l2r, atomic;
+  size_t tiles_off;   // BatchTile offset in the tile table
+  int ntiles;
+};
+
+bool same_ops(const std::vector<sf_batch_op> &a, const sf_batch_op *b, int32_t n) {
+  if (int32_t(a.size()) != n) return false;
+  for (int32_t i = 0; i < n; ++i)
+    if (memcmp(&a[i], &b[i], sizeof(sf_batch_op)) != 0) return false;
+  return true;
+}
+
+}  // namespace
+
+struct sf_batch_s {
+  std::vector<sf_batch_op> ops;    // the list the device tables were built for
+  std::vector<int32_t> modes, paths;   // forests' resolved choices at build time
+  DevBuf tables;
+  const TsArgs *ts_ops = nullptr;
+  const RmArgs *rm_ops = nullptr;
+  const BatchTile *tiles = nullptr;
+  std::vector<Group> groups;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+void drop_graph(sf_batch_t *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Decide each operation's kernel variant and arguments, group them, upload the tables.
+int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
+  std::vector<TsArgs> ts;
+  std::vector<RmArgs> rm;
+  std::vector<BatchTile> tiles;
+  std::map<std::tuple<int, int, int, int, int, int, int, int>, std::vector<BatchTile>> grouped;
+  std::vector<int32_t> modes(n, 0), paths(n, 0);
+  int stage = 0;
+  std::vector<std::pair<int, const sf_t *>> reduce_seen;   // (stage, forest) with fold scratch in use
+  for (int32_t i = 0; i < n; ++i) {
+    const sf_batch_op &o = ops[i];
+    if (o.kind == SF_OP_BARRIER) {
+      ++stage;
+      continue;
+    }
+    sf_t *sf = o.sf;
+    int rc;
+    if (!sf) return SF_ERR_NULL;
+    if (!sf->setup) return SF_ERR_STATE;
+    if ((rc = check_unit(o.unit, o.op))) return rc;
+    if (o.kind != SF_OP_BCAST && o.kind != SF_OP_REDUCE) return SF_ERR_ARG;
+    const int w = elem_size(o.unit.dtype), ub = w * o.unit.bs;
+    const void *root = o.kind == SF_OP_BCAST ? o.src : o.dst;
+    const void *leaf = o.kind == SF_OP_BCAST ? o.dst : o.src;
+    if ((sf->info.nroots_total && (rc = check_ptr(root, w))) || (sf->info.leaf_extent_total && (rc = check_ptr(leaf, w))))
+      return rc;
+    if (sf->info.nedges == 0) continue;
+    if (o.kind == SF_OP_BCAST) {
+      const int path = bcast_path(sf);
+      paths[i] = path;
+      const int vb = pick_vb(w, ub, true, {root, leaf});
+      if (!vb) return SF_ERR_ALIGN;
+      const int vbo = o.op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+      if (path == SF_PATH_ROOT_MAJOR) {
+        const int idx = int(rm.size());
+        rm.push_back(rm_args(sf, sf->dp.rm_fold_tiles, sf->dp.n_rm_fold_tiles, const_cast<void *>(root),
+                             const_cast<void *>(leaf), nullptr, ub / vbo));
+        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_BCAST, 0, 0}];
+        for (int32_t t = 0; t < sf->dp.n_rm_fold_tiles; ++t) g.push_back(BatchTile{idx, t});
+      } else {   // fused (the three-phase path is not batched)
+        const int idx = int(ts.size());
+        ts.push_back(ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, root, const_cast<void *>(leaf), nullptr, ub / vbo,
+                             PH_FUSED));
+        auto &g = grouped[{stage, 0, o.unit.dtype, o.op, vbo, 0, 0, 0}];
+        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, t});
+      }
+    } else {
+      const int mode = reduce_mode(sf);
+      modes[i] = mode;
+      const bool atomic = mode == SF_MODE_ATOMIC && o.op != SF_REPLACE && o.unit.dtype != SF_BF16;
+      if (atomic) {
+        const int idx = int(ts.size());
+        ts.push_back(ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, const_cast<void *>(root), nullptr, o.unit.bs,
+                             PH_FUSED));
+        auto &g = grouped[{stage, 0, o.unit.dtype, o.op, w, 0, 1, 1}];
+        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, t});
+      } else {
+        const int vb = pick_vb(w, ub, true, {root, leaf});
+        if (!vb) return SF_ERR_ALIGN;
+        const int vbo = o.op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
+        const int nv = ub / vbo;
+        if (o.op != SF_REPLACE && sf->dp.n_partial_slots > 0) {
+          for (auto &p : reduce_seen)
+            if (p.first == stage && p.second == sf) return SF_ERR_ARG;   // one fold scratch per forest
+          reduce_seen.push_back({stage, sf});
+          const size_t pbytes = size_t(sf->dp.n_partial_slots) * nv * acc_pack_bytes(o.unit.dtype, o.op, vbo);
+          const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
+          if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
+        }
+        const RmTile *rt = o.op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
+        const int nt = o.op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+        const int idx = int(rm.size());
+        rm.push_back(rm_args(sf, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
+        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, 0, 0}];
+        for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, t});
+      }
+    }
+  }
+  // rm_args captured the forests' scratch pointers before any ensure() above could move them:
+  // refresh them now that every scratch buffer has its final size
+  for (int32_t i = 0, r = 0; i < n; ++i) {
+    const sf_batch_op &o = ops[i];
+    if (o.kind == SF_OP_BARRIER || o.sf->info.nedges == 0) continue;
+    const bool is_rm = (o.kind == SF_OP_BCAST && paths[i] == SF_PATH_ROOT_MAJOR) ||
+                       (o.kind == SF_OP_REDUCE &&
+                        !(modes[i] == SF_MODE_ATOMIC && o.op != SF_REPLACE && o.unit.dtype != SF_BF16));
+    if (is_rm) {
+      rm[r].partial = o.sf->partial.p;
+      rm[r].counter = static_cast<int32_t *>(o.sf->counter.p);
+      ++r;
+    }
+  }
+  b->groups.clear();
+  for (auto &kv : grouped) {
+    const auto &k = kv.first;
+    Group g{};
+    g.stage = std::get<0>(k);
+    g.family = std::get<1>(k);
+    g.dtype = std::get<2>(k);
+    g.op = std::get<3>(k);
+    g.vb = std::get<4>(k);
+    g.mode = std::get<5>(k);
+    g.l2r = std::get<6>(k);
+    g.atomic = std::get<7>(k);
+    g.tiles_off = tiles.size();
+    g.ntiles = int(kv.second.size());
+    tiles.insert(tiles.end(), kv.second.begin(), kv.second.end());
+    b->groups.push_back(g);
+  }
+  // upload: [TsArgs][RmArgs][BatchTile], 256-byte aligned pieces
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_ts = 0, o_rm = al(ts.size() * sizeof(TsArgs)), o_t = o_rm + al(rm.size() * sizeof(RmArgs));
+  const size_t bytes = std::max<size_t>(o_t + tiles.size() * sizeof(BatchTile), 256);
+  std::vector<char> host(bytes, 0);
+  if (!ts.empty()) memcpy(host.data() + o_ts, ts.data(), ts.size() * sizeof(TsArgs));
+  if (!rm.empty()) memcpy(host.data() + o_rm, rm.data(), rm.size() * sizeof(RmArgs));
+  if (!tiles.empty()) memcpy(host.data() + o_t, tiles.data(), tiles.size() * sizeof(BatchTile));
+  int rc;
+  if (b->tables.bytes < bytes) {
+    if ((rc = cuda_err(cudaStreamSynchronize(s)))) return rc;
+    release(b->tables);
+    if ((rc = ensure(b->tables, bytes, false, s))) return rc;
+  }
+  if ((rc = cuda_err(cudaMemcpyAsync(b->tables.p, host.data(), bytes, cudaMemcpyHostToDevice, s)))) return rc;
+  if ((rc = cuda_err(cudaStreamSynchronize(s)))) return rc;   // `host` dies at return
+  char *base = static_cast<char *>(b->tables.p);
+  b->ts_ops = reinterpret_cast<const TsArgs *>(base + o_ts);
+  b->rm_ops = reinterpret_cast<const RmArgs *>(base + o_rm);
+  b->tiles = reinterpret_cast<const BatchTile *>(base + o_t);
+  b->ops.assign(ops, ops + n);
+  b->modes = modes;
+  b->paths = paths;
+  return SF_SUCCESS;
+}
+
+int launch_groups(sf_batch_t *b, cudaStream_t s) {
+  for (const Group &g : b->groups) {
+    cudaError_t e;
+    if (g.family == 0)
+      e = launch_ts(g.dtype, g.op, g.vb, g.l2r, g.atomic, false, TsLaunch{nullptr, b->ts_ops, b->tiles + g.tiles_off, g.ntiles, s});
+    else
+      e = launch_rm(g.dtype, g.op, g.vb, g.mode, RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s});
+    int rc;
+    if ((rc = launched(e))) return rc;
+  }
+  return SF_SUCCESS;
+}
+
+// the forests' current choices differ from those the tables were built with
+bool choices_changed(const sf_batch_t *b) {
+  for (size_t i = 0; i < b->ops.size(); ++i) {
+    const sf_batch_op &o = b->ops[i];
+    if (o.kind == SF_OP_BCAST && bcast_path(o.sf) != b->paths[i]) return true;
+    if (o.kind == SF_OP_REDUCE && reduce_mode(o.sf) != b->modes[i]) return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sf_batch_create(sf_batch_t **out) {
+  if (!out) return SF_ERR_NULL;
+  *out = new (std::nothrow) sf_batch_t();
+  return *out ? SF_SUCCESS : SF_ERR_ALLOC;
+}
+
+int sf_batch_run(sf_batch_t *b, const sf_batch_op ops[], int32_t n, int32_t use_graph, sf_stream_t stream) {
+  if (!b || (n > 0 && !ops)) return SF_ERR_NULL;
+  if (n < 0) return SF_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc;
+  if (!same_ops(b->ops, ops, n) || choices_changed(b)) {
+    drop_graph(b);
+    if ((rc = build(b, ops, n, s))) {
+      b->ops.clear();
+      return rc;
+    }
+  }
+  if (!use_graph) return launch_groups(b, s);
+  if (!b->exec) {
+    if (!b->capture_stream && (rc = cuda_err(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking))))
+      return rc;
+    if ((rc = cuda_err(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)))) return rc;
+    const int lrc = launch_groups(b, b->capture_stream);
+    // captured launches run only when the graph is launched: count them there
+    launch_counter().fetch_sub(int64_t(b->groups.size()), std::memory_order_relaxed);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (lrc) {
+      if (graph) cudaGraphDestroy(graph);
+      return lrc;
+    }
+    if ((rc = cuda_err(ec))) return rc;
+    b->graph = graph;
+    if ((rc = cuda_err(cudaGraphInstantiate(&b->exec, b->graph, 0)))) {
+      drop_graph(b);
+      return rc;
+    }
+  }
+  if ((rc = cuda_err(cudaGraphLaunch(b->exec, s)))) return rc;
+  launch_counter().fetch_add(int64_t(b->groups.size()), std::memory_order_relaxed);
+  return SF_SUCCESS;
+}
+
+int sf_batch_launches(const sf_batch_t *b, int32_t *launches) {
+  if (!b || !launches) return SF_ERR_NULL;
+  *launches = int32_t(b->groups.size());
+  return SF_SUCCESS;
+}
+
+int sf_batch_destroy(sf_batch_t *b) {
+  if (!b) return SF_SUCCESS;
+  drop_graph(b);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  release(b->tables);
+  delete b;
+  return SF_SUCCESS;
+}
+
+// Time the candidate data paths (Bcast) or modes (Reduce) on a scratch copy of the output and
+// keep the fastest as what SF_PATH_AUTO / SF_MODE_AUTO mean for this forest.
+int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst, int32_t op, int32_t reps,
+                sf_stream_t stream, int32_t *choice) {
+  int rc;
+  if (!sf) return SF_ERR_NULL;
+  if (!sf->setup) return SF_ERR_STATE;
+  if ((rc = check_unit(unit, op))) return rc;
+  if (kind != SF_OP_BCAST && kind != SF_OP_REDUCE) return SF_ERR_ARG;
+  if (reps < 1) reps = 3;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ub = size_t(elem_size(unit.dtype)) * unit.bs;
+  const size_t bytes = ub * size_t(kind == SF_OP_BCAST ? sf->info.leaf_extent_total : sf->info.nroots_total);
+  DevBuf scratch;
+  if ((rc = ensure(scratch, std::max<size_t>(bytes, 256), false, s))) return rc;
+  std::vector<int32_t> cands;
+  if (kind == SF_OP_BCAST) cands = {SF_PATH_FUSED, SF_PATH_ROOT_MAJOR, SF_PATH_THREE_PHASE};
+  else if (op == SF_REPLACE || unit.dtype == SF_BF16) cands = {SF_MODE_DETERMINISTIC};
+  else cands = {SF_MODE_DETERMINISTIC, SF_MODE_ATOMIC};
+  cudaEvent_t e0, e1;
+  if ((rc = cuda_err(cudaEventCreate(&e0)))) { release(scratch); return rc; }
+  if ((rc = cuda_err(cudaEventCreate(&e1)))) { cudaEventDestroy(e0); release(scratch); return rc; }
+  float best = 1e30f;
+  int32_t best_c = cands[0];
+  for (int32_t c : cands) {
+    float total = 0.f;
+    for (int r = 0; r <= reps && !rc; ++r) {   // first round warms up
+      if (bytes) rc = cuda_err(cudaMemcpyAsync(scratch.p, dst, bytes, cudaMemcpyDeviceToDevice, s));
+      if (!rc) rc = cuda_err(cudaEventRecord(e0, s));
+      if (!rc) rc = kind == SF_OP_BCAST ? bcast_all(sf, unit, src, scratch.p, op, s, c)
+                                        : reduce_all(sf, unit, src, scratch.p, op, s, c);
+      if (!rc) rc = cuda_err(cudaEventRecord(e1, s));
+      if (!rc) rc = cuda_err(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      if (!rc) rc = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) total += ms;
+    }
+    if (rc) break;
+    if (total < best) {
+      best = total;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release(scratch);
+  if (rc) return rc;
+  if (kind == SF_OP_BCAST) sf->tuned_path = best_c;
+  else sf->tuned_mode = best_c;
+  if (choice) *choice = best_c;
+  return SF_SUCCESS;
+}
+
+}  // extern "C"

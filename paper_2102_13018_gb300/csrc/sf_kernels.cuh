@@ -764,4 +764,30 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>
   rm_tile<T, VB, OP, MODE>(a, t);
 }
 
+// ------------------------------------------------------------------ batched launches
+// Many forests' operations of one kernel variant in one launch: each CTA takes one
+// (operation, tile) pair and runs that forest's tile with that operation's arguments.
+struct BatchTile {
+  int32_t op;     // index into the operation table
+  int32_t tile;   // tile of that operation's forest
+};
+
+template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, ATOMIC>::value))
+    ts_batch_kernel(const TsArgs *ops, const BatchTile *tiles) {
+  const BatchTile bt = tiles[blockIdx.x];
+  const TsArgs a = ops[bt.op];
+  const TsTile t = a.tiles[bt.tile];
+  ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
+}
+
+template <typename T, int VB, int OP, int MODE>
+__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>::value))
+    rm_batch_kernel(const RmArgs *ops, const BatchTile *tiles) {
+  const BatchTile bt = tiles[blockIdx.x];
+  const RmArgs a = ops[bt.op];
+  const RmTile t = a.tiles[bt.tile];
+  rm_tile<T, VB, OP, MODE>(a, t);
+}
+
 }  // namespace sfgb

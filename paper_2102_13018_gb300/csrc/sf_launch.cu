@@ -6,44 +6,39 @@ namespace sfgb {
 
 namespace {
 template <int VB, bool L2R>
-cudaError_t ts_copy(const TsArgs &a, int ntiles, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
+cudaError_t ts_copy(const TsLaunch &L) {
   using T = typename std::conditional<VB == 2, unsigned short, unsigned int>::type;
-  ts_kernel<T, VB, OP_REPLACE, L2R, false, false><<<ntiles, kThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  return go_ts<T, VB, OP_REPLACE, L2R, false, false>(L);
 }
 template <int VB>
-cudaError_t rm_copy(int mode, const RmArgs &a, int ntiles, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
+cudaError_t rm_copy(int mode, const RmLaunch &L) {
   using T = typename std::conditional<VB == 2, unsigned short, unsigned int>::type;
   switch (mode) {
-    case RM_REDUCE: rm_kernel<T, VB, OP_REPLACE, RM_REDUCE><<<ntiles, kThreads, 0, s>>>(a); break;
-    case RM_BCAST: rm_kernel<T, VB, OP_REPLACE, RM_BCAST><<<ntiles, kThreads, 0, s>>>(a); break;
-    case RM_FETCH: rm_kernel<T, VB, OP_REPLACE, RM_FETCH><<<ntiles, kThreads, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    case RM_REDUCE: return go_rm<T, VB, OP_REPLACE, RM_REDUCE>(L);
+    case RM_BCAST: return go_rm<T, VB, OP_REPLACE, RM_BCAST>(L);
+    case RM_FETCH: return go_rm<T, VB, OP_REPLACE, RM_FETCH>(L);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 }  // namespace
 
-cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsArgs &a, int ntiles,
-                      cudaStream_t s) {
+cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsLaunch &L) {
   if (op == OP_REPLACE && !atomic) {   // a copy: independent of the dtype
     switch (vb) {
-      case 2: return l2r ? ts_copy<2, true>(a, ntiles, s) : ts_copy<2, false>(a, ntiles, s);
-      case 4: return l2r ? ts_copy<4, true>(a, ntiles, s) : ts_copy<4, false>(a, ntiles, s);
-      case 8: return l2r ? ts_copy<8, true>(a, ntiles, s) : ts_copy<8, false>(a, ntiles, s);
-      case 16: return l2r ? ts_copy<16, true>(a, ntiles, s) : ts_copy<16, false>(a, ntiles, s);
+      case 2: return l2r ? ts_copy<2, true>(L) : ts_copy<2, false>(L);
+      case 4: return l2r ? ts_copy<4, true>(L) : ts_copy<4, false>(L);
+      case 8: return l2r ? ts_copy<8, true>(L) : ts_copy<8, false>(L);
+      case 16: return l2r ? ts_copy<16, true>(L) : ts_copy<16, false>(L);
     }
     return cudaErrorInvalidValue;
   }
   if (!atomic && l2r) return cudaErrorInvalidValue;   // leaf->root with an op needs atomics
   switch (dtype) {
-    case SF_INT32: return launch_ts_ops_t<int32_t>(op, vb, atomic, fetch, a, ntiles, s);
-    case SF_INT64: return launch_ts_ops_t<int64_t>(op, vb, atomic, fetch, a, ntiles, s);
-    case SF_FP32: return launch_ts_ops_t<float>(op, vb, atomic, fetch, a, ntiles, s);
-    case SF_FP64: return launch_ts_ops_t<double>(op, vb, atomic, fetch, a, ntiles, s);
-    case SF_BF16: return launch_ts_ops_t<bf16>(op, vb, atomic, fetch, a, ntiles, s);
+    case SF_INT32: return launch_ts_ops_t<int32_t>(op, vb, atomic, fetch, L);
+    case SF_INT64: return launch_ts_ops_t<int64_t>(op, vb, atomic, fetch, L);
+    case SF_FP32: return launch_ts_ops_t<float>(op, vb, atomic, fetch, L);
+    case SF_FP64: return launch_ts_ops_t<double>(op, vb, atomic, fetch, L);
+    case SF_BF16: return launch_ts_ops_t<bf16>(op, vb, atomic, fetch, L);
   }
   return cudaErrorInvalidValue;
 }
@@ -60,22 +55,22 @@ cudaError_t launch_move(int vb, const MoveArgs &a, int ntiles, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s) {
+cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmLaunch &L) {
   if (op == OP_REPLACE) {
     switch (vb) {
-      case 2: return rm_copy<2>(mode, a, ntiles, s);
-      case 4: return rm_copy<4>(mode, a, ntiles, s);
-      case 8: return rm_copy<8>(mode, a, ntiles, s);
-      case 16: return rm_copy<16>(mode, a, ntiles, s);
+      case 2: return rm_copy<2>(mode, L);
+      case 4: return rm_copy<4>(mode, L);
+      case 8: return rm_copy<8>(mode, L);
+      case 16: return rm_copy<16>(mode, L);
     }
     return cudaErrorInvalidValue;
   }
   switch (dtype) {
-    case SF_INT32: return launch_rm_t<int32_t>(op, vb, mode, a, ntiles, s);
-    case SF_INT64: return launch_rm_t<int64_t>(op, vb, mode, a, ntiles, s);
-    case SF_FP32: return launch_rm_t<float>(op, vb, mode, a, ntiles, s);
-    case SF_FP64: return launch_rm_t<double>(op, vb, mode, a, ntiles, s);
-    case SF_BF16: return launch_rm_t<bf16>(op, vb, mode, a, ntiles, s);
+    case SF_INT32: return launch_rm_t<int32_t>(op, vb, mode, L);
+    case SF_INT64: return launch_rm_t<int64_t>(op, vb, mode, L);
+    case SF_FP32: return launch_rm_t<float>(op, vb, mode, L);
+    case SF_FP64: return launch_rm_t<double>(op, vb, mode, L);
+    case SF_BF16: return launch_rm_t<bf16>(op, vb, mode, L);
   }
   return cudaErrorInvalidValue;
 }

@@ -8,19 +8,41 @@
 
 namespace sfgb {
 
+// A launch of one kernel variant: either one forest (`single`, passed by value) or a batch
+// (`ops` and `tiles` are device tables, one CTA per (operation, tile) pair).
+struct TsLaunch {
+  const TsArgs *single;
+  const TsArgs *ops;
+  const BatchTile *tiles;
+  int ntiles;
+  cudaStream_t s;
+};
+struct RmLaunch {
+  const RmArgs *single;
+  const RmArgs *ops;
+  const BatchTile *tiles;
+  int ntiles;
+  cudaStream_t s;
+};
+
 // dtype codes are the SF_* codes of sf.h
 // Two-sided kernel: REPLACE copies (any dtype, vector width vb in {2,4,8,16}), plain ops for
 // Bcast (l2r = false), atomics for Reduce / FetchAndOp (l2r = true, vb = element size).
-cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsArgs &a,
-                      int ntiles, cudaStream_t s);
+cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsLaunch &L);
+cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmLaunch &L);
 cudaError_t launch_move(int vb, const MoveArgs &a, int ntiles, cudaStream_t s);
-cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
 
+inline cudaError_t launch_ts(int dtype, int op, int vb, bool l2r, bool atomic, bool fetch, const TsArgs &a,
+                             int ntiles, cudaStream_t s) {
+  return launch_ts(dtype, op, vb, l2r, atomic, fetch, TsLaunch{&a, nullptr, nullptr, ntiles, s});
+}
+inline cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s) {
+  return launch_rm(dtype, op, vb, mode, RmLaunch{&a, nullptr, nullptr, ntiles, s});
+}
 
 // per-dtype instantiations (one translation unit each)
-template <typename T> cudaError_t launch_rm_t(int op, int vb, int mode, const RmArgs &a, int ntiles, cudaStream_t s);
-template <typename T>
-cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsArgs &a, int ntiles, cudaStream_t s);
+template <typename T> cudaError_t launch_rm_t(int op, int vb, int mode, const RmLaunch &L);
+template <typename T> cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsLaunch &L);
 
 // accumulator pack bytes of the fold for (dtype, op, vb): scratch sizing
 int acc_pack_bytes(int dtype, int op, int vb);

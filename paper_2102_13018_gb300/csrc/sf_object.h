@@ -1,0 +1,82 @@
+// sf_object.h -- the forest object behind sf_t and helpers shared by the ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <initializer_list>
+#include <vector>
+
+#include "sf.h"
+#include "sf_host.h"
+#include "sf_launch.h"
+
+namespace sfgb {
+
+enum { K_BCAST = 1, K_REDUCE = 2, K_FETCH = 3, K_BCAST_MT = 4, K_REDUCE_MT = 5 };
+
+struct Pending {
+  int kind;
+  sf_unit unit;
+  const void *p0, *p1, *p2;
+  int32_t op;
+  int32_t m0, m1;      // memtypes (memtype calls)
+  int32_t finish;      // work left for End: 0 none, 1 three-phase unpack
+};
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+inline int elem_size(int dtype) {
+  switch (dtype) {
+    case SF_INT32: case SF_FP32: return 4;
+    case SF_INT64: case SF_FP64: return 8;
+    case SF_BF16: return 2;
+  }
+  return 0;
+}
+
+}  // namespace sfgb
+
+struct sf_s {
+  sfgb::Graph g;
+  sfgb::HostPlan hp;
+  sf_info info{};
+  bool setup = false;
+  int device = -1;
+  sfgb::DevBuf blob;                 // all plan arrays
+  sfgb::DevPlan dp{};
+  std::vector<sfgb::Tile> h_move_tiles;
+  const sfgb::Tile *move_tiles = nullptr;
+  int32_t n_move_tiles = 0;
+  sfgb::DevBuf partial, counter;     // fold scratch
+  sfgb::DevBuf rootbuf, leafbuf;     // three-phase buffers
+  sfgb::DevBuf stage_root, stage_leaf;   // memtype staging
+  int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
+  int32_t tuned_mode = SF_MODE_DETERMINISTIC;   // what AUTO means (sf_autotune may change it)
+  int32_t tuned_path = SF_PATH_FUSED;
+  std::vector<sfgb::Pending> pending;
+};
+
+namespace sfgb {
+
+std::atomic<int64_t> &launch_counter();
+int cuda_err(cudaError_t e);
+int ensure(DevBuf &b, size_t bytes, bool zero, cudaStream_t s);
+void release(DevBuf &b);
+int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs);
+int check_unit(const sf_unit &u, int32_t op);
+int check_ptr(const void *p, int w);
+int launched(cudaError_t e);
+TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *src, void *dst, void *upd, int nv,
+               int phase);
+RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv);
+int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC after resolving AUTO
+int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO
+// Enqueue a whole operation (begin and end) on `s`; used by sf_autotune.
+int bcast_all(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s, int path);
+int reduce_all(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int mode);
+
+}  // namespace sfgb

@@ -229,6 +229,68 @@ class StarForest:
         return rootdata
 
 
+    # ---------------------------------------------------------------- autotuner
+    def autotune(self, kind: str, src, dst, op: str, bs=None, reps: int = 3, stream=None) -> str:
+        """Time the Bcast data paths (kind "bcast") or Reduce modes (kind "reduce") and make
+        the fastest what "auto" means for this forest.  src/dst are not modified."""
+        root = src if kind == "bcast" else dst
+        u = self._unit(root, self.nroots_total, bs)
+        k = _abi.SF_OP_BCAST if kind == "bcast" else _abi.SF_OP_REDUCE
+        c = ctypes.c_int32()
+        check(self._lib.sf_autotune(self._h, u, k, self._ptr(src), self._ptr(dst), OPS[op], reps,
+                                    self._stream(stream), ctypes.byref(c)), "sf_autotune")
+        names = {v: n for n, v in (PATHS if kind == "bcast" else MODES).items()}
+        return names[c.value]
+
+
+class Batch:
+    """Many forests' Bcast / Reduce operations in few launches (optionally one CUDA graph)."""
+
+    def __init__(self):
+        self._lib = _abi.load()
+        h = ctypes.c_void_p()
+        check(self._lib.sf_batch_create(ctypes.byref(h)), "sf_batch_create")
+        self._h = h
+        self._ops = None
+        self._keep = None
+
+    def set_ops(self, ops):
+        """ops: list of ("bcast"|"reduce", StarForest, op, src, dst, bs) or "barrier"."""
+        arr = (_abi.sf_batch_op * len(ops))()
+        keep = []
+        for i, o in enumerate(ops):
+            if o == "barrier":
+                arr[i].kind = _abi.SF_OP_BARRIER
+                continue
+            kind, sf, op, src, dst, bs = o
+            root = src if kind == "bcast" else dst
+            arr[i].sf = sf._h
+            arr[i].kind = _abi.SF_OP_BCAST if kind == "bcast" else _abi.SF_OP_REDUCE
+            arr[i].unit = sf._unit(root, sf.nroots_total, bs)
+            arr[i].op = OPS[op]
+            arr[i].src = src.data_ptr()
+            arr[i].dst = dst.data_ptr()
+            keep.append((sf, src, dst))
+        self._ops, self._keep = arr, keep
+        return self
+
+    def run(self, use_graph: bool = False, stream=None):
+        check(self._lib.sf_batch_run(self._h, self._ops, len(self._ops), int(use_graph),
+                                     StarForest._stream(stream)), "sf_batch_run")
+
+    def launches(self) -> int:
+        n = ctypes.c_int32()
+        check(self._lib.sf_batch_launches(self._h, ctypes.byref(n)), "sf_batch_launches")
+        return n.value
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._lib.sf_batch_destroy(self._h)
+        except Exception:
+            pass
+
+
 def launch_count() -> int:
     """Kernels libsfgb has launched in this process."""
     return int(_abi.load().sf_launch_count())

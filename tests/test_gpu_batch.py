@@ -1,0 +1,137 @@
+"""Batched execution and the autotuner vs the oracle and vs one call per forest (GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+import sfgen
+from tests.gpu_util import assert_atomic_sum_close, assert_bits_equal, make_data, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2102_13018_gb300 import Batch, SFError, StarForest, launch_count  # noqa: E402
+
+FORESTS = sfgen.cfg4_batched(nforests=24, lo=1e2, hi=2e4)
+
+
+def build(forests, modes=None):
+    items = []
+    for i, f in enumerate(forests):
+        dt, bs, op = f.meta["dtype"], f.meta["bs"], f.meta["op"]
+        sf = StarForest.from_forest(f).setup()
+        if modes is not None:
+            sf.set_mode(modes[i % len(modes)])
+        else:
+            sf.set_mode("deterministic")
+        root, leaf = make_data(f, dt, bs, 1000 + i)
+        items.append(dict(f=f, sf=sf, dt=dt, bs=bs, op=op, root=root, leaf=leaf))
+    return items
+
+
+def ops_for(items):
+    bc = [("bcast", it["sf"], it["op"], it["r"], it["l"], it["bs"]) for it in items]
+    rd = [("reduce", it["sf"], it["op"], it["l2"], it["r2"], it["bs"]) for it in items]
+    return bc + ["barrier"] + rd
+
+
+def fresh(items):
+    for it in items:
+        it["r"], it["l"] = to_dev(it["root"], it["dt"]), to_dev(it["leaf"], it["dt"])
+        it["r2"], it["l2"] = to_dev(it["root"], it["dt"]), to_dev(it["leaf"], it["dt"])
+
+
+def check(items, atomic=False):
+    for it in items:
+        f, dt, bs, op = it["f"], it["dt"], it["bs"], it["op"]
+        want_l = oracle.bcast(f, dt, bs, it["root"], it["leaf"], op)
+        assert_bits_equal(to_host(it["l"], dt), want_l, f"batch bcast {f.name} {op} {dt}x{bs}")
+        want_r = oracle.reduce(f, dt, bs, it["leaf"], it["root"], op)
+        got = to_host(it["r2"], dt)
+        if atomic and op == "SUM" and dt.startswith("fp"):
+            assert_atomic_sum_close(got, want_r, f, dt, bs, it["leaf"], it["root"], f"batch reduce {f.name}")
+        else:
+            assert_bits_equal(got, want_r, f"batch reduce {f.name} {op} {dt}x{bs}")
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_oracle(use_graph):
+    items = build(FORESTS)
+    fresh(items)
+    b = Batch().set_ops(ops_for(items))
+    n0 = launch_count()
+    b.run(use_graph=use_graph)
+    torch.cuda.synchronize()
+    check(items)
+    assert 0 < b.launches() < 2 * len(items)       # 2 operations per forest, grouped by variant
+    assert launch_count() - n0 == b.launches()
+    # a second run with the same list reuses the tables (and the graph): reset data first
+    for it in items:
+        it["r"].copy_(to_dev(it["root"], it["dt"]))
+        it["l"].copy_(to_dev(it["leaf"], it["dt"]))
+        it["r2"].copy_(to_dev(it["root"], it["dt"]))
+        it["l2"].copy_(to_dev(it["leaf"], it["dt"]))
+    b.run(use_graph=use_graph)
+    torch.cuda.synchronize()
+    check(items)
+
+
+def test_batch_atomic_and_root_major_mix():
+    items = build(FORESTS[:12], modes=["atomic", "deterministic"])
+    for i, it in enumerate(items):
+        it["sf"].set_path("root_major" if i % 3 == 0 else "fused")
+    fresh(items)
+    Batch().set_ops(ops_for(items)).run(use_graph=True)
+    torch.cuda.synchronize()
+    check(items, atomic=True)
+
+
+def test_batch_equals_one_call_per_forest():
+    items = build(FORESTS[:10])
+    fresh(items)
+    Batch().set_ops(ops_for(items)).run()
+    torch.cuda.synchronize()
+    for it in items:
+        r, l = to_dev(it["root"], it["dt"]), to_dev(it["leaf"], it["dt"])
+        it["sf"].bcast(r, l, it["op"], bs=it["bs"])
+        l2 = to_dev(it["leaf"], it["dt"])
+        it["sf"].reduce(l2, r, it["op"], bs=it["bs"])
+        want_root = it["root"].copy()
+        want = oracle.reduce(it["f"], it["dt"], it["bs"], it["leaf"], want_root, it["op"])
+        assert_bits_equal(to_host(r, it["dt"]), want, "per-forest reduce")
+        assert_bits_equal(to_host(it["r2"], it["dt"]), to_host(r, it["dt"]), "batch == per-forest")
+
+
+def test_batch_errors():
+    items = build(FORESTS[:2])
+    fresh(items)
+    it = items[0]
+    b = Batch()
+    b.set_ops([("reduce", it["sf"], it["op"], it["l2"], it["r2"], it["bs"])])
+    b._ops[0].sf = None
+    with pytest.raises(SFError) as e:
+        b.run()
+    assert e.value.name == "SF_ERR_NULL"
+
+
+@pytest.mark.parametrize("kind", ["bcast", "reduce"])
+def test_autotune_choice_is_valid_and_auto_stays_correct(kind):
+    f = sfgen.cfg3_spmv(1 << 15, 4)
+    sf = StarForest.from_forest(f).setup()
+    root, leaf = make_data(f, "fp64", 1, 1100)
+    r, l = to_dev(root, "fp64"), to_dev(leaf, "fp64")
+    if kind == "bcast":
+        choice = sf.autotune("bcast", r, l, "REPLACE")
+        assert choice in ("fused", "root_major", "three_phase")
+        assert_bits_equal(to_host(l, "fp64"), leaf, "autotune leaves dst untouched")
+        sf.set_path("auto").bcast(r, l, "REPLACE")
+        assert_bits_equal(to_host(l, "fp64"), oracle.bcast(f, "fp64", 1, root, leaf, "REPLACE"), "auto bcast")
+    else:
+        choice = sf.autotune("reduce", l, r, "SUM")
+        assert choice in ("deterministic", "atomic")
+        assert_bits_equal(to_host(r, "fp64"), root, "autotune leaves dst untouched")
+        sf.set_mode("auto").reduce(l, r, "SUM")
+        want = oracle.reduce(f, "fp64", 1, leaf, root, "SUM")
+        assert_atomic_sum_close(to_host(r, "fp64"), want, f, "fp64", 1, leaf, root, "auto reduce")
