@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-forests", type=int, default=512)
     return ap.parse_args()
 
 
@@ -204,6 +206,68 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args, stream, flush):
+    """512 uneven forests (Zipf in-degree, mixed dtype / bs / op), each doing one Bcast and one
+    Reduce: one library call per forest and operation vs one batched run (variant-grouped
+    launches) vs the batched run replayed as one CUDA graph."""
+    import numpy as np
+    import torch
+    import sfgen
+    from paper_2102_13018_gb300 import Batch, StarForest
+    tdt = {"fp32": torch.float32, "fp64": torch.float64, "int64": torch.int64}
+    forests = sfgen.cfg4_batched(nforests=args.batch_forests)
+    items, nbytes, edges = [], 0, 0
+    for i, f in enumerate(forests):
+        sf = StarForest.from_forest(f).setup().set_mode("deterministic")
+        dt, bs = tdt[f.meta["dtype"]], f.meta["bs"]
+        r = (torch.rand(sf.nroots_total * bs, device="cuda") * 100).to(dt)
+        l = (torch.rand(sf.leaf_extent * bs, device="cuda") * 100).to(dt)
+        r2, l2 = r.clone(), l.clone()
+        info = sf.info()
+        ub = bs * r.element_size()
+        idx = 4 * (info["edges_one_indexed"] + 2 * info["edges_two_indexed"])
+        nbytes += ub * info["connected_roots"] + ub * info["nedges"] + idx      # Bcast
+        nbytes += ub * info["nedges"] + 2 * ub * info["connected_roots"] + idx  # Reduce
+        edges += info["nedges"]
+        items.append((sf, f.meta["op"], r, l, r2, l2, bs))
+    ops = [("bcast", sf, op, r, l, bs) for sf, op, r, l, r2, l2, bs in items] + ["barrier"] + \
+          [("reduce", sf, op, l2, r2, bs) for sf, op, r, l, r2, l2, bs in items]
+
+    def per_forest():
+        for sf, op, r, l, r2, l2, bs in items:
+            sf.bcast(r, l, op, bs=bs, stream=stream)
+        for sf, op, r, l, r2, l2, bs in items:
+            sf.reduce(l2, r2, op, bs=bs, stream=stream)
+
+    batch = Batch().set_ops(ops)
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    t_per = timed(per_forest)
+    t_batch = timed(lambda: batch.run(use_graph=False, stream=stream))
+    t_graph = timed(lambda: batch.run(use_graph=True, stream=stream))
+    return {"workload": f"{len(items)} forests, nleaves log-uniform in [1e2,1e6], Zipf(1.1) in-degree, "
+                        f"fp32/fp64/int64, bs in {{1,2,3,8}}, op in {{SUM,MAX,REPLACE}}; Bcast then Reduce each",
+            "edges": int(edges), "algorithmic_bytes": int(nbytes),
+            "per_forest_ms": t_per, "batched_ms": t_batch, "graph_ms": t_graph,
+            "launches_per_forest_path": 2 * len(items), "launches_batched": batch.launches(),
+            "per_forest_gbs": nbytes / (t_per * 1e-3) / 1e9, "batched_gbs": nbytes / (t_batch * 1e-3) / 1e9,
+            "graph_gbs": nbytes / (t_graph * 1e-3) / 1e9, "speedup_graph_vs_per_forest": t_per / t_graph}
+
+
 def host_info(forest):
     """Plan statistics from the library's host setup pass (no GPU needed)."""
     from paper_2102_13018_gb300 import StarForest
@@ -359,6 +423,10 @@ def main():
         e2e = {"value": world * (bb + rb) / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -374,7 +442,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "ops": ops, "variants": variants,
+                "clocks": clk, "ops": ops, "variants": variants, "batched": batched,
                 "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
                                               "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
                                               "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}

@@ -196,6 +196,19 @@ int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, cons
 int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
                                int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
 
+/* Reduce MAX with location, for the gradient of Reduce MAX.  For every root with leaves,
+ * rootdata = the maximum over its leaves (the old root value takes no part) and argleaf = the
+ * leaf unit (index into leafdata's units) of the first leaf in canonical order that reaches it,
+ * per component; argleaf is int32[nroots_total * bs].  Roots without leaves are not written
+ * (initialise rootdata and argleaf, e.g. to 0 and -1).  No NaN in leafdata. */
+int sf_reduce_maxloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t *argleaf,
+                     sf_stream_t stream);
+
+/* Gradient of sf_reduce_maxloc: leafgrad[argleaf[i]*bs + c] = rootgrad[i] for every root
+ * element i = r*bs + c with argleaf[i] >= 0; other leaf elements are not written. */
+int sf_maxloc_scatter(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
+                      sf_stream_t stream);
+
 /* ---- Batched execution (Sec. V.D: launch cost and pipelining; CUDA graphs as future work) ----
  * A batch runs many forests' operations with few kernel launches: operations are grouped by
  * kernel variant (element type, op, vector width, data path, Reduce mode) and each group is one

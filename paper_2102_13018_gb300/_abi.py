@@ -94,6 +94,8 @@ def load():
                  "sf_reduce_with_memtype_begin", "sf_reduce_with_memtype_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, i32, vp, i32, vp, i32, vp]
     lib.sf_reduce_noalloc.argtypes = [vp, sf_unit, vp, vp, i32, vp]
+    lib.sf_reduce_maxloc.argtypes = [vp, sf_unit, vp, vp, vp, vp]
+    lib.sf_maxloc_scatter.argtypes = [vp, sf_unit, vp, vp, vp, vp]
     lib.sf_batch_create.argtypes = [P(vp)]
     lib.sf_batch_run.argtypes = [vp, P(sf_batch_op), i32, i32, vp]
     lib.sf_batch_launches.argtypes = [vp, P(i32)]

@@ -554,6 +554,7 @@ int sf_destroy(sf_t *sf) {
     release(sf->blob);
     release(sf->partial);
     release(sf->counter);
+    release(sf->partial_arg);
     release(sf->rootbuf);
     release(sf->leafbuf);
     release(sf->stage_root);
@@ -561,6 +562,51 @@ int sf_destroy(sf_t *sf) {
   }
   delete sf;
   return SF_SUCCESS;
+}
+
+int sf_reduce_maxloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t *argleaf,
+                     sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, SF_MAX))) return rc;
+  const int w = elem_size(unit.dtype);
+  if (sf->info.nroots_total && ((rc = check_ptr(rootdata, w)) || (rc = check_ptr(argleaf, 4)))) return rc;
+  if (sf->info.leaf_extent_total && (rc = check_ptr(leafdata, w))) return rc;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (sf->dp.n_partial_slots > 0) {
+    const size_t slots = size_t(sf->dp.n_partial_slots) * unit.bs;
+    if ((rc = ensure(sf->partial, slots * w, false, s)) || (rc = ensure(sf->partial_arg, slots * 4, false, s)) ||
+        (rc = ensure(sf->counter, size_t(sf->dp.n_counters) * unit.bs * 4, true, s)))
+      return rc;
+  }
+  MaxlocArgs a{};
+  a.mask = sf->dp.mask;
+  a.pr_root = sf->dp.pr_root;
+  a.pr_leaf = sf->dp.pr_leaf;
+  a.m_leaf = sf->dp.m_leaf;
+  a.blocks = sf->dp.blocks;
+  a.combs = sf->dp.combs;
+  a.tiles = sf->dp.rm_fold_tiles;
+  a.out = rootdata;
+  a.leaf = leafdata;
+  a.arg = argleaf;
+  a.partial = sf->partial.p;
+  a.partial_arg = static_cast<int32_t *>(sf->partial_arg.p);
+  a.counter = static_cast<int32_t *>(sf->counter.p);
+  a.bs = unit.bs;
+  return launched(launch_maxloc(unit.dtype, a, sf->dp.n_rm_fold_tiles, s));
+}
+
+int sf_maxloc_scatter(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
+                      sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, SF_MAX))) return rc;
+  const int w = elem_size(unit.dtype);
+  if (sf->info.nroots_total && ((rc = check_ptr(argleaf, 4)) || (rc = check_ptr(rootgrad, w)))) return rc;
+  if (sf->info.leaf_extent_total && (rc = check_ptr(leafgrad, w))) return rc;
+  const int64_t n = sf->info.nroots_total * int64_t(unit.bs);
+  return launched(launch_maxloc_scatter(unit.dtype, argleaf, rootgrad, leafgrad, n, unit.bs,
+                                        static_cast<cudaStream_t>(stream)));
 }
 
 const char *sf_error_string(int code) {

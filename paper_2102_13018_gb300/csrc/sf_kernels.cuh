@@ -764,6 +764,107 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>
   rm_tile<T, VB, OP, MODE>(a, t);
 }
 
+// ------------------------------------------------------------------ MAX with location
+// out[root] = max over the root's leaves (not combined with out's old value) and arg[root] =
+// the leaf unit of the first leaf in canonical order that reaches it, per component; roots
+// without leaves are left alone.  Ties keep the earlier leaf: strict "greater" inside a block,
+// and blocks of one root are combined in block order by the last arriver.
+struct MaxlocArgs {
+  const uint32_t *mask;
+  const int32_t *pr_root, *pr_leaf;
+  const int32_t *m_leaf;
+  const Block *blocks;
+  const Comb *combs;
+  const RmTile *tiles;
+  void *out;            // max values, units of bs elements
+  const void *leaf;
+  int32_t *arg;         // leaf unit per (root, component)
+  void *partial;        // scratch values of multi-block roots
+  int32_t *partial_arg; // scratch leaf units of multi-block roots
+  int32_t *counter;
+  int32_t bs;
+};
+
+template <typename T> __device__ __forceinline__ bool greater(T a, T b) { return a > b; }
+template <> __device__ __forceinline__ bool greater<bf16>(bf16 a, bf16 b) {
+  return __bfloat162float(a) > __bfloat162float(b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) maxloc_kernel(MaxlocArgs a) {
+  const RmTile t = a.tiles[blockIdx.x];
+  const T *leaf = static_cast<const T *>(a.leaf);
+  T *out = static_cast<T *>(a.out);
+  const int32_t bs = a.bs;
+  const int32_t work = t.cnt * bs;
+  if (t.kind == T_MASKED || t.kind == T_PAIRS) {
+    for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+      const int32_t k = w / bs, c = w - k * bs;
+      int64_t ru, lu;
+      if (t.kind == T_MASKED) {
+        const int64_t bit = t.mask0 + t.k0 + k;
+        if (!((a.mask[bit >> 5] >> (bit & 31)) & 1u)) continue;
+        ru = t.root0 + t.k0 + k;
+        lu = t.leaf0 + t.k0 + k;
+      } else {
+        ru = a.pr_root[t.a + k];
+        lu = a.pr_leaf[t.a + k];
+      }
+      out[ru * bs + c] = leaf[lu * bs + c];
+      a.arg[ru * bs + c] = int32_t(lu);
+    }
+  } else if (t.kind == T_CHUNKS) {
+    for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+      const int32_t cl = w / bs, c = w - cl * bs;
+      const Block b = a.blocks[t.a + cl];
+      int32_t best_l = a.m_leaf[b.e0];
+      T best = leaf[int64_t(best_l) * bs + c];
+      for (int32_t e = 1; e < b.n; ++e) {
+        const int32_t l = a.m_leaf[b.e0 + e];
+        const T y = leaf[int64_t(l) * bs + c];
+        if (greater(y, best)) { best = y; best_l = l; }
+      }
+      const int64_t ri = int64_t(b.root) * bs + c;
+      if (b.comb < 0) {
+        out[ri] = best;
+        a.arg[ri] = best_l;
+        continue;
+      }
+      const Comb cb = a.combs[b.comb];
+      const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;
+      const int64_t slot = (int64_t(cb.slot) + ci) * bs + c;
+      __stcg(static_cast<T *>(a.partial) + slot, best);
+      __stcg(a.partial_arg + slot, best_l);
+      __threadfence();
+      int32_t *ctr = a.counter + int64_t(cb.ctr) * bs + c;
+      if (atomicAdd(ctr, 1) == cb.nch - 1) {
+        __threadfence();
+        T v = __ldcg(static_cast<const T *>(a.partial) + int64_t(cb.slot) * bs + c);
+        int32_t l = __ldcg(a.partial_arg + int64_t(cb.slot) * bs + c);
+        for (int32_t i = 1; i < cb.nch; ++i) {
+          const int64_t si = (int64_t(cb.slot) + i) * bs + c;
+          const T y = __ldcg(static_cast<const T *>(a.partial) + si);
+          if (greater(y, v)) { v = y; l = __ldcg(a.partial_arg + si); }
+        }
+        out[ri] = v;
+        a.arg[ri] = l;
+        *ctr = 0;
+      }
+    }
+  }
+}
+
+// grad_leaf[arg[i] * bs + c] = grad_root[i] for every root element i = r * bs + c with arg >= 0
+// (each leaf belongs to one root, so no two elements write the same place).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) maxloc_scatter_kernel(const int32_t *arg, const T *grad_root,
+                                                                  T *grad_leaf, int64_t n, int32_t bs) {
+  for (int64_t i = blockIdx.x * int64_t(kThreads) + threadIdx.x; i < n; i += int64_t(gridDim.x) * kThreads) {
+    const int32_t l = arg[i];
+    if (l >= 0) grad_leaf[int64_t(l) * bs + (i % bs)] = grad_root[i];
+  }
+}
+
 // ------------------------------------------------------------------ batched launches
 // Many forests' operations of one kernel variant in one launch: each CTA takes one
 // (operation, tile) pair and runs that forest's tile with that operation's arguments.

@@ -75,6 +75,29 @@ cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmLaunch &L) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, cudaStream_t s) {
+  switch (dtype) {
+    case SF_INT32: return launch_maxloc_t<int32_t>(a, ntiles, s);
+    case SF_INT64: return launch_maxloc_t<int64_t>(a, ntiles, s);
+    case SF_FP32: return launch_maxloc_t<float>(a, ntiles, s);
+    case SF_FP64: return launch_maxloc_t<double>(a, ntiles, s);
+    case SF_BF16: return launch_maxloc_t<bf16>(a, ntiles, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_maxloc_scatter(int dtype, const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n,
+                                  int32_t bs, cudaStream_t s) {
+  switch (dtype) {
+    case SF_INT32: return launch_maxloc_scatter_t<int32_t>(arg, grad_root, grad_leaf, n, bs, s);
+    case SF_INT64: return launch_maxloc_scatter_t<int64_t>(arg, grad_root, grad_leaf, n, bs, s);
+    case SF_FP32: return launch_maxloc_scatter_t<float>(arg, grad_root, grad_leaf, n, bs, s);
+    case SF_FP64: return launch_maxloc_scatter_t<double>(arg, grad_root, grad_leaf, n, bs, s);
+    case SF_BF16: return launch_maxloc_scatter_t<bf16>(arg, grad_root, grad_leaf, n, bs, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 int acc_pack_bytes(int dtype, int op, int vb) {
   const int w = (dtype == SF_INT32 || dtype == SF_FP32) ? 4 : (dtype == SF_BF16 ? 2 : 8);
   const int lanes = vb / w;

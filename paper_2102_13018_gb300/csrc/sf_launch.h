@@ -44,6 +44,15 @@ inline cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmArgs &
 template <typename T> cudaError_t launch_rm_t(int op, int vb, int mode, const RmLaunch &L);
 template <typename T> cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsLaunch &L);
 
+// MAX with location and its gradient scatter (per dtype)
+cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, cudaStream_t s);
+cudaError_t launch_maxloc_scatter(int dtype, const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n,
+                                  int32_t bs, cudaStream_t s);
+template <typename T> cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, cudaStream_t s);
+template <typename T>
+cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n, int32_t bs,
+                                    cudaStream_t s);
+
 // accumulator pack bytes of the fold for (dtype, op, vb): scratch sizing
 int acc_pack_bytes(int dtype, int op, int vb);
 

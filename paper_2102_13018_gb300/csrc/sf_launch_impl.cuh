@@ -82,8 +82,29 @@ cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsLau
   return cudaErrorInvalidValue;
 }
 
-#define SFGB_INSTANTIATE(T)                                                      \
-  template cudaError_t launch_rm_t<T>(int, int, int, const RmLaunch &);          \
-  template cudaError_t launch_ts_ops_t<T>(int, int, bool, bool, const TsLaunch &);
+template <typename T>
+cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  maxloc_kernel<T><<<ntiles, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n, int32_t bs,
+                                    cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  const int grid = int(blocks < 152 * 16 ? blocks : 152 * 16);
+  maxloc_scatter_kernel<T><<<grid, kThreads, 0, s>>>(arg, static_cast<const T *>(grad_root),
+                                                     static_cast<T *>(grad_leaf), n, bs);
+  return cudaGetLastError();
+}
+
+#define SFGB_INSTANTIATE(T)                                                                            \
+  template cudaError_t launch_rm_t<T>(int, int, int, const RmLaunch &);                                \
+  template cudaError_t launch_ts_ops_t<T>(int, int, bool, bool, const TsLaunch &);                     \
+  template cudaError_t launch_maxloc_t<T>(const MaxlocArgs &, int, cudaStream_t);                      \
+  template cudaError_t launch_maxloc_scatter_t<T>(const int32_t *, const void *, void *, int64_t, int32_t, \
+                                                  cudaStream_t);
 
 }  // namespace sfgb

@@ -52,6 +52,7 @@ struct sf_s {
   const sfgb::Tile *move_tiles = nullptr;
   int32_t n_move_tiles = 0;
   sfgb::DevBuf partial, counter;     // fold scratch
+  sfgb::DevBuf partial_arg;          // MAX-with-location scratch (leaf units of block maxima)
   sfgb::DevBuf rootbuf, leafbuf;     // three-phase buffers
   sfgb::DevBuf stage_root, stage_leaf;   // memtype staging
   int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;

@@ -229,6 +229,19 @@ class StarForest:
         return rootdata
 
 
+    def reduce_maxloc(self, leafdata, rootdata, argleaf, bs=None, stream=None):
+        """rootdata = max over each root's leaves, argleaf = first leaf reaching it (int32)."""
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_reduce_maxloc(self._h, u, self._ptr(leafdata), self._ptr(rootdata), self._ptr(argleaf),
+                                         self._stream(stream)), "sf_reduce_maxloc")
+        return rootdata, argleaf
+
+    def maxloc_scatter(self, argleaf, rootgrad, leafgrad, bs=None, stream=None):
+        u = self._unit(rootgrad, self.nroots_total, bs)
+        check(self._lib.sf_maxloc_scatter(self._h, u, self._ptr(argleaf), self._ptr(rootgrad), self._ptr(leafgrad),
+                                          self._stream(stream)), "sf_maxloc_scatter")
+        return leafgrad
+
     # ---------------------------------------------------------------- autotuner
     def autotune(self, kind: str, src, dst, op: str, bs=None, reps: int = 3, stream=None) -> str:
         """Time the Bcast data paths (kind "bcast") or Reduce modes (kind "reduce") and make
