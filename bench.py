@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-pingpong", action="store_true")
     ap.add_argument("--batch-forests", type=int, default=512)
     return ap.parse_args()
 
@@ -268,6 +269,78 @@ def run_batched(args, stream, flush):
             "graph_gbs": nbytes / (t_graph * 1e-3) / 1e9, "speedup_graph_vs_per_forest": t_per / t_graph}
 
 
+def run_pingpong(stream):
+    """Sec. VI.A ping-pong on one GPU: n fp64 roots on rank 0 connected consecutively to n leaves
+    on rank 1; one round trip is Bcast REPLACE then Reduce REPLACE (the roots come back
+    unchanged).  Median round-trip latency per message size, launched one call at a time and
+    replayed as a CUDA graph.  The paper's Table I (Summit V100s, CUDA-aware MPI, two GPUs) is
+    context only: here nothing leaves the GPU."""
+    import torch
+    import sfgen
+    from paper_2102_13018_gb300 import StarForest
+    out = {}
+    for nbytes in (1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22):
+        n = nbytes // 8
+        sf = StarForest.from_forest(sfgen.pingpong(n)).setup().set_mode("deterministic")
+        x = torch.rand(n, dtype=torch.float64, device="cuda")
+        lv = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+        def trip():
+            sf.bcast(x, lv, "REPLACE")
+            sf.reduce(lv, x, "REPLACE")
+
+        for _ in range(20):
+            trip()
+        torch.cuda.synchronize()
+        reps = 200
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            trip()
+        e1.record()
+        torch.cuda.synchronize()
+        plain_us = e0.elapsed_time(e1) * 1e3 / reps
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            trip()
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g):
+            for _ in range(10):
+                trip()
+        for _ in range(5):
+            g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps // 10):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = e0.elapsed_time(e1) * 1e3 / reps
+        out[f"{nbytes // 1024}K"] = {"plain_us": plain_us, "graph_us": graph_us}
+    return {"what": "round trip Bcast REPLACE + Reduce REPLACE, contiguous 2-rank forest, fp64, one GPU",
+            "paper_table1_sf_dd_us": {"1K": 22.8, "4K": 23.0, "16K": 22.9, "64K": 23.5, "256K": 27.7,
+                                      "1024K": 46.3, "4096K": 111.8},
+            "sizes": out}
+
+
+def max_over_ranks(local_ms: float, world: int, device: str = "cpu") -> float:
+    """Slowest rank's timed total (every rank runs an independent replica)."""
+    import torch
+    if world <= 1:
+        return float(local_ms)
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_step: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job GB/s: all replicas' algorithmic bytes over the slowest rank's time."""
+    return world * bytes_per_step * steps / (max_ms * 1e-3) / 1e9
+
+
 def host_info(forest):
     """Plan statistics from the library's host setup pass (no GPU needed)."""
     from paper_2102_13018_gb300 import StarForest
@@ -347,12 +420,9 @@ def main():
     bcast_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
     reduce_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     total_ms = sum(bcast_ms) + sum(reduce_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(total_ms, world, "cuda")
     bb, rb = algorithmic_bytes(info)
-    value = world * (bb + rb) * K / (max_ms * 1e-3) / 1e9
+    value = job_value(bb + rb, K, max_ms, world)
     peak, peak_src = measured_peak()
     b_avg, r_avg = statistics.mean(bcast_ms), statistics.mean(reduce_ms)
     dom = ("rm_kernel", rb, r_avg) if r_avg >= b_avg else ("ts_kernel", bb, b_avg)
@@ -423,6 +493,10 @@ def main():
         e2e = {"value": world * (bb + rb) / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke}
 
+    pingpong = None
+    if not args.no_pingpong:
+        pingpong = run_pingpong(stream)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(args, stream, flush)
@@ -443,6 +517,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "ops": ops, "variants": variants, "batched": batched,
+                "pingpong": pingpong,
                 "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
                                               "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
                                               "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}

@@ -196,6 +196,31 @@ int sf_reduce_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t leafmtype, cons
 int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const void *leafdata,
                                int32_t rootmtype, void *rootdata, int32_t op, sf_stream_t stream);
 
+/* ---- Forests derived from a forest (Sec. III.B-C) ----
+ * Embedded forests (PetscSFCreateEmbeddedRootSF / LeafSF): only the edges of the selected
+ * roots (global root units, i.e. rootoff[p] + r) or selected leaves (global leaf units), with
+ * nothing renumbered: the new forest has the same ranks, roots and leaf layout, so the
+ * original rootdata / leafdata buffers serve it.  *out is a new forest (set it up before use;
+ * destroy it with sf_destroy).  Errors: SF_ERR_NULL, SF_ERR_ARG, SF_ERR_RANGE, SF_ERR_ALLOC. */
+int sf_create_embedded_root_sf(const sf_t *sf, int64_t n, const int64_t selected_roots[], sf_t **out);
+int sf_create_embedded_leaf_sf(const sf_t *sf, int64_t n, const int64_t selected_leaves[], sf_t **out);
+
+/* Multi-forest (PetscSFGetMultiSF): every root of degree d becomes d roots, and the k-th leaf of
+ * a root in canonical order connects to its k-th new root.  Built on first use with the
+ * paper's recipe -- Reduce SUM of ones for the degrees, roots set to their rank's degree prefix
+ * sums, FetchAndOp SUM with leaves of 1, each leaf fetching its new root's offset -- which
+ * allocates and synchronises `stream`.  *multi is owned by sf (valid until sf_destroy; do not
+ * destroy it).  Rank p of the multi-forest owns sum of its roots' degrees roots. */
+int sf_get_multi_sf(sf_t *sf, sf_stream_t stream, sf_t **multi);
+
+/* Gather (PetscSFGatherBegin/End): multirootdata[k-th new root of r] = leafdata[k-th leaf of r]
+ * (multirootdata has the multi-forest's root layout).  Scatter reverses it.  Both are
+ * Reduce / Bcast REPLACE over the multi-forest, with the same begin/end rules. */
+int sf_gather_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *multirootdata, sf_stream_t stream);
+int sf_gather_end(sf_t *sf, sf_unit unit, const void *leafdata, void *multirootdata, sf_stream_t stream);
+int sf_scatter_begin(sf_t *sf, sf_unit unit, const void *multirootdata, void *leafdata, sf_stream_t stream);
+int sf_scatter_end(sf_t *sf, sf_unit unit, const void *multirootdata, void *leafdata, sf_stream_t stream);
+
 /* Reduce MAX with location, for the gradient of Reduce MAX.  For every root with leaves,
  * rootdata = the maximum over its leaves (the old root value takes no part) and argleaf = the
  * leaf unit (index into leafdata's units) of the first leaf in canonical order that reaches it,

@@ -95,6 +95,11 @@ def load():
         getattr(lib, name).argtypes = [vp, sf_unit, i32, vp, i32, vp, i32, vp]
     lib.sf_reduce_noalloc.argtypes = [vp, sf_unit, vp, vp, i32, vp]
     lib.sf_reduce_maxloc.argtypes = [vp, sf_unit, vp, vp, vp, vp]
+    lib.sf_create_embedded_root_sf.argtypes = [vp, i64, P(i64), P(vp)]
+    lib.sf_create_embedded_leaf_sf.argtypes = [vp, i64, P(i64), P(vp)]
+    lib.sf_get_multi_sf.argtypes = [vp, vp, P(vp)]
+    for name in ("sf_gather_begin", "sf_gather_end", "sf_scatter_begin", "sf_scatter_end"):
+        getattr(lib, name).argtypes = [vp, sf_unit, vp, vp, vp]
     lib.sf_maxloc_scatter.argtypes = [vp, sf_unit, vp, vp, vp, vp]
     lib.sf_batch_create.argtypes = [P(vp)]
     lib.sf_batch_run.argtypes = [vp, P(sf_batch_op), i32, i32, vp]

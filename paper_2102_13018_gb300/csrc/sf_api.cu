@@ -550,6 +550,11 @@ int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const 
 int sf_destroy(sf_t *sf) {
   if (!sf) return SF_SUCCESS;
   if (!sf->pending.empty()) return SF_ERR_PENDING;
+  if (sf->multi) {
+    const int rc = sf_destroy(sf->multi);
+    if (rc) return rc;
+    sf->multi = nullptr;
+  }
   if (sf->setup) {
     release(sf->blob);
     release(sf->partial);

@@ -42,6 +42,12 @@ struct HostPlan {
 int build_graph(int32_t nranks, const int64_t nroots[], const int64_t nleaves[],
                 const int64_t *const ilocal[], const sf_node *const iremote[], Graph &g);
 
+// Same, with each rank's leaf extent given (at least max(ilocal)+1): a derived forest keeps the
+// buffer layout of the forest it came from.
+int build_graph_extents(int32_t nranks, const int64_t nroots[], const int64_t nleaves[],
+                        const int64_t *const ilocal[], const sf_node *const iremote[], const int64_t extents[],
+                        Graph &g);
+
 // The setup pass: two-sided grouping, pattern detection, root-major plan, statistics.
 int analyze(const Graph &g, HostPlan &plan, sf_info &info);
 

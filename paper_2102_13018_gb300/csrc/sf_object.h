@@ -59,6 +59,7 @@ struct sf_s {
   int32_t tuned_mode = SF_MODE_DETERMINISTIC;   // what AUTO means (sf_autotune may change it)
   int32_t tuned_path = SF_PATH_FUSED;
   std::vector<sfgb::Pending> pending;
+  sf_t *multi = nullptr;             // multi-forest, built on first use (Gather / Scatter)
 };
 
 namespace sfgb {

@@ -91,6 +91,21 @@ int build_graph(int32_t P, const int64_t nroots[], const int64_t nleaves[],
   return SF_SUCCESS;
 }
 
+int build_graph_extents(int32_t P, const int64_t nroots[], const int64_t nleaves[], const int64_t *const ilocal[],
+                        const sf_node *const iremote[], const int64_t extents[], Graph &g) {
+  const int rc = build_graph(P, nroots, nleaves, ilocal, iremote, g);
+  if (rc != SF_SUCCESS || !extents) return rc;
+  for (int32_t q = 0; q < P; ++q) {
+    const int64_t own = g.leafoff[q + 1] - g.leafoff[q];
+    if (extents[q] < own) return SF_ERR_RANGE;
+  }
+  for (int32_t q = 0; q < P; ++q) {
+    g.leafoff[q + 1] = g.leafoff[q] + extents[q];
+    if (g.leafoff[q + 1] > kMaxUnits) return SF_ERR_TOO_LARGE;
+  }
+  return SF_SUCCESS;
+}
+
 namespace {
 
 struct RunBuilder {

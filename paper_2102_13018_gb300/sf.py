@@ -87,6 +87,26 @@ class StarForest:
         self.leaf_extent = int(lo[-1])
 
     @classmethod
+    def _wrap(cls, handle, owned: bool = True) -> "StarForest":
+        """A StarForest around an existing handle (derived forests)."""
+        self = cls.__new__(cls)
+        self._lib = _abi.load()
+        self._h = handle
+        self._owned = owned
+        inf = sf_info()
+        check(self._lib.sf_get_info(self._h, ctypes.byref(inf)), "sf_get_info")
+        P = inf.nranks
+        self.nranks = P
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ro = np.zeros(P + 1, np.int64)
+        lo = np.zeros(P + 1, np.int64)
+        check(self._lib.sf_get_layout(self._h, ro.ctypes.data_as(i64p), lo.ctypes.data_as(i64p)), "sf_get_layout")
+        self.rootoff, self.leafoff = ro, lo
+        self.nroots_total = int(ro[-1])
+        self.leaf_extent = int(lo[-1])
+        return self
+
+    @classmethod
     def from_forest(cls, f) -> "StarForest":
         """From any object with nroots, nleaves, ilocal, iremote_rank, iremote_index."""
         return cls(f.nroots, f.nleaves, f.ilocal, f.iremote_rank, f.iremote_index)
@@ -114,16 +134,55 @@ class StarForest:
         return self
 
     def destroy(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owned", True):
             check(self._lib.sf_destroy(self._h), "sf_destroy")
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
-            if getattr(self, "_h", None):
+            if getattr(self, "_h", None) and getattr(self, "_owned", True):
                 self._lib.sf_destroy(self._h)
         except Exception:
             pass
+
+    # ---------------------------------------------------------------- derived forests
+    def embedded_roots(self, selected) -> "StarForest":
+        """Forest of the edges of the selected roots (global root units), same layout."""
+        sel = np.ascontiguousarray(selected, dtype=np.int64)
+        h = ctypes.c_void_p()
+        check(self._lib.sf_create_embedded_root_sf(self._h, sel.size, sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                   ctypes.byref(h)), "sf_create_embedded_root_sf")
+        return StarForest._wrap(h)
+
+    def embedded_leaves(self, selected) -> "StarForest":
+        """Forest of the edges of the selected leaves (global leaf units), same layout."""
+        sel = np.ascontiguousarray(selected, dtype=np.int64)
+        h = ctypes.c_void_p()
+        check(self._lib.sf_create_embedded_leaf_sf(self._h, sel.size, sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                   ctypes.byref(h)), "sf_create_embedded_leaf_sf")
+        return StarForest._wrap(h)
+
+    def multi_sf(self, stream=None) -> "StarForest":
+        """The multi-forest (owned by this forest)."""
+        h = ctypes.c_void_p()
+        check(self._lib.sf_get_multi_sf(self._h, self._stream(stream), ctypes.byref(h)), "sf_get_multi_sf")
+        return StarForest._wrap(h, owned=False)
+
+    def gather(self, leafdata, multirootdata, bs=None, stream=None):
+        m = self.multi_sf(stream)
+        u = self._unit(multirootdata, m.nroots_total, bs)
+        args = (self._h, u, self._ptr(leafdata), self._ptr(multirootdata), self._stream(stream))
+        check(self._lib.sf_gather_begin(*args), "sf_gather_begin")
+        check(self._lib.sf_gather_end(*args), "sf_gather_end")
+        return multirootdata
+
+    def scatter(self, multirootdata, leafdata, bs=None, stream=None):
+        m = self.multi_sf(stream)
+        u = self._unit(multirootdata, m.nroots_total, bs)
+        args = (self._h, u, self._ptr(multirootdata), self._ptr(leafdata), self._stream(stream))
+        check(self._lib.sf_scatter_begin(*args), "sf_scatter_begin")
+        check(self._lib.sf_scatter_end(*args), "sf_scatter_end")
+        return leafdata
 
     # ---------------------------------------------------------------- helpers
     @staticmethod

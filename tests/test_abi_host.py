@@ -158,3 +158,20 @@ def test_setup_without_a_device_reports_cuda_error():
     with pytest.raises(SFError) as ei:
         sf.setup(stream=0)
     assert ei.value.name == "SF_ERR_CUDA"
+
+
+def test_embedded_root_and_leaf_forests_keep_the_layout():
+    """Sec. III.C: removing edges renumbers nothing; Fig. 2 with root (1,0) (unit 3) selected
+    keeps edges e1, e2, e8; with leaf units {0, 5} selected keeps e0 and e5."""
+    sf = StarForest.from_forest(sfgen.fig2())
+    er = sf.embedded_roots([3])
+    assert np.array_equal(er.rootoff, sf.rootoff) and np.array_equal(er.leafoff, sf.leafoff)
+    info = er.analyze().info()
+    assert info["nedges"] == 3 and info["max_in_degree"] == 3 and info["connected_roots"] == 1
+    el = sf.embedded_leaves([0, 5])
+    assert np.array_equal(el.leafoff, sf.leafoff)
+    assert el.analyze().info()["nedges"] == 2
+    with pytest.raises(SFError) as e:
+        sf.embedded_roots([9])
+    assert e.value.name == "SF_ERR_RANGE"
+    assert sf.embedded_roots([]).analyze().info()["nedges"] == 0

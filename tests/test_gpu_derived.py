@@ -1,0 +1,93 @@
+"""Multi-forest, Gather / Scatter and embedded forests on the GPU (Sec. III.B-C)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sfgen
+from tests import npref
+from tests.gpu_util import assert_bits_equal, make_data, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2102_13018_gb300 import StarForest  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig2.json")))
+
+
+def test_fig2_multi_forest_sizes_and_gather():
+    sf = StarForest.from_forest(sfgen.fig2()).setup()
+    m = sf.multi_sf()
+    assert m.rootoff.tolist() == [0, 3, 8, 10]          # degrees per rank: 2+0+1, 3+0+1+1, 1+1
+    assert np.array_equal(m.leafoff, sf.leafoff)
+    leaf = torch.arange(11, dtype=torch.int32, device="cuda") * 10
+    multi = torch.full((10,), -1, dtype=torch.int32, device="cuda")
+    sf.gather(leaf, multi)
+    # leaf unit of each edge and its new root offset: the FetchAndOp leafupdate of Fig. 2
+    upd = [v for rank in GOLD["fetch_and_op_sum"]["leafupdate"] for v in rank]
+    want = np.full(10, -1)
+    lo = sf.leafoff
+    ro = m.rootoff
+    for q, rank_upd in enumerate(GOLD["fetch_and_op_sum"]["leafupdate"]):
+        for l, off in enumerate(rank_upd):
+            if off == -7:       # isolated leaf
+                continue
+            p = sfgen.fig2().iremote_rank[q][list(sfgen.fig2().ilocal[q]).index(l)]
+            want[ro[p] + off] = (lo[q] + l) * 10
+    assert multi.cpu().numpy().tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("f", [sfgen.cfg1_plain_tiny(), sfgen.zipf_forest(9, 4, 50000, 2000, 4),
+                               sfgen.random_forest(61, 6, 300, 400)], ids=lambda f: f.name)
+def test_gather_then_scatter_round_trip(f):
+    sf = StarForest.from_forest(f).setup()
+    m = sf.multi_sf()
+    L, R = npref.edge_arrays(f)
+    deg = np.bincount(R, minlength=sf.nroots_total)
+    assert m.nroots_total == len(L) and m.nroots_total == int(deg.sum())
+    _, leaf = make_data(f, "fp64", 3, 1400)
+    multi = torch.zeros(m.nroots_total * 3, dtype=torch.float64, device="cuda")
+    sf.gather(to_dev(leaf, "fp64"), multi, bs=3)
+    # every new root holds one leaf's unit; as a multiset per original root they are its leaves
+    back = to_dev(np.zeros_like(leaf), "fp64")
+    sf.scatter(multi, back, bs=3)
+    connected = np.zeros(sf.leaf_extent, bool)
+    connected[L] = True
+    got = to_host(back, "fp64").reshape(-1, 3)
+    assert np.array_equal(got[connected], leaf.reshape(-1, 3)[connected])
+    assert np.all(got[~connected] == 0)
+    # new roots of root r are its leaves in canonical order
+    mh = multi.cpu().numpy().reshape(-1, 3)
+    order = np.argsort(R, kind="stable")
+    ro_m = m.rootoff
+    # rank-major new roots: rank p holds, for its roots in order, their leaves in canonical order
+    assert np.array_equal(mh, leaf.reshape(-1, 3)[L[order]])
+
+
+@pytest.mark.parametrize("f", [sfgen.cfg3_spmv(1 << 15, 4), sfgen.random_forest(62, 4, 200, 300)],
+                         ids=lambda f: f.name)
+def test_embedded_root_forest_moves_only_selected_roots(f):
+    sf = StarForest.from_forest(f).setup()
+    sel = np.arange(0, sf.nroots_total, 3)
+    er = sf.embedded_roots(sel).setup()
+    root, leaf = make_data(f, "fp64", 1, 1500)
+    full = oracle.bcast(f, "fp64", 1, root, leaf, "REPLACE")
+    L, R = npref.edge_arrays(f)
+    keep = np.isin(R, sel)
+    want = leaf.copy()
+    want[L[keep]] = full[L[keep]]
+    l = to_dev(leaf, "fp64")
+    er.bcast(to_dev(root, "fp64"), l, "REPLACE")
+    assert_bits_equal(to_host(l, "fp64"), want, "embedded bcast")
+    # Reduce over the embedded forest: unselected roots unchanged
+    r = to_dev(root, "fp64")
+    er.set_mode("deterministic").reduce(to_dev(leaf, "fp64"), r, "SUM")
+    got = to_host(r, "fp64")
+    unsel = np.setdiff1d(np.arange(sf.nroots_total), sel)
+    assert np.array_equal(got[unsel], root[unsel])

@@ -205,3 +205,22 @@ def test_launch_counter_advances():
     n0 = launch_count()
     sf.bcast(to_dev(root, "fp64"), to_dev(leaf, "fp64"))
     assert launch_count() > n0
+
+
+@pytest.mark.parametrize("nbytes", [1 << 10, 1 << 16, 1 << 22])
+def test_pingpong_round_trip_restores_roots(nbytes):
+    """Sec. VI.A: Bcast REPLACE to rank 1, Reduce REPLACE back; the contiguous pattern on both
+    sides means no index array is read."""
+    n = nbytes // 8
+    f = sfgen.pingpong(n)
+    sf = StarForest.from_forest(f).setup()
+    info = sf.info()
+    assert info["edges_both_pattern"] == n
+    x0 = torch.rand(n, dtype=torch.float64, device="cuda")
+    x = x0.clone()
+    lv = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        sf.bcast(x, lv, "REPLACE")
+        x.zero_()
+        sf.reduce(lv, x, "REPLACE")
+    assert torch.equal(x, x0)
