@@ -22,13 +22,35 @@ DTYPE_NAMES = {"int32": _abi.SF_INT32, "int64": _abi.SF_INT64, "fp32": _abi.SF_F
                "bf16": _abi.SF_BF16}
 
 
+_TORCH_CODES = None
+_CURRENT_STREAM = None
+
+
 def _torch_dtype_code(t) -> int:
-    import torch
-    m = {torch.int32: _abi.SF_INT32, torch.int64: _abi.SF_INT64, torch.float32: _abi.SF_FP32,
-         torch.float64: _abi.SF_FP64, torch.bfloat16: _abi.SF_BF16}
-    if t.dtype not in m:
+    global _TORCH_CODES
+    if _TORCH_CODES is None:
+        import torch
+        _TORCH_CODES = {torch.int32: _abi.SF_INT32, torch.int64: _abi.SF_INT64, torch.float32: _abi.SF_FP32,
+                        torch.float64: _abi.SF_FP64, torch.bfloat16: _abi.SF_BF16}
+    code = _TORCH_CODES.get(t.dtype)
+    if code is None:
         raise TypeError(f"unsupported dtype {t.dtype}")
-    return m[t.dtype]
+    return code
+
+
+def _current_stream_handle() -> int:
+    """The current torch CUDA stream's handle, or 0 (legacy default stream) without CUDA."""
+    global _CURRENT_STREAM
+    if _CURRENT_STREAM is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                _CURRENT_STREAM = lambda: torch.cuda.current_stream().cuda_stream  # noqa: E731
+            else:
+                return 0
+        except Exception:
+            return 0
+    return _CURRENT_STREAM()
 
 
 def _numpy_dtype_code(a: np.ndarray, bf16: bool = False) -> int:
@@ -188,13 +210,7 @@ class StarForest:
     @staticmethod
     def _stream(stream):
         if stream is None:
-            try:
-                import torch
-                if torch.cuda.is_available() and torch.cuda.is_initialized():
-                    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-            except Exception:
-                pass
-            return ctypes.c_void_p(0)
+            return ctypes.c_void_p(_current_stream_handle())
         if isinstance(stream, int):
             return ctypes.c_void_p(stream)
         return ctypes.c_void_p(stream.cuda_stream)
@@ -230,8 +246,10 @@ class StarForest:
                                      self._stream(stream)), "sf_bcast_end")
 
     def bcast(self, rootdata, leafdata, op: str = "REPLACE", bs: Optional[int] = None, stream=None):
-        self.bcast_begin(rootdata, leafdata, op, bs, stream)
-        self.bcast_end(rootdata, leafdata, op, bs, stream)
+        args = (self._h, self._unit(rootdata, self.nroots_total, bs), self._ptr(rootdata), self._ptr(leafdata),
+                OPS[op], self._stream(stream))
+        check(self._lib.sf_bcast_begin(*args), "sf_bcast_begin")
+        check(self._lib.sf_bcast_end(*args), "sf_bcast_end")
         return leafdata
 
     def reduce_begin(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
@@ -245,8 +263,10 @@ class StarForest:
                                       self._stream(stream)), "sf_reduce_end")
 
     def reduce(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
-        self.reduce_begin(leafdata, rootdata, op, bs, stream)
-        self.reduce_end(leafdata, rootdata, op, bs, stream)
+        args = (self._h, self._unit(rootdata, self.nroots_total, bs), self._ptr(leafdata), self._ptr(rootdata),
+                OPS[op], self._stream(stream))
+        check(self._lib.sf_reduce_begin(*args), "sf_reduce_begin")
+        check(self._lib.sf_reduce_end(*args), "sf_reduce_end")
         return rootdata
 
     def fetch_and_op_begin(self, rootdata, leafdata, leafupdate, op: str = "SUM", bs=None, stream=None):
