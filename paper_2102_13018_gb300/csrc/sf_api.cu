@@ -299,7 +299,7 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
                o_tst = b.add(h.ts_tiles), o_tss = b.add(h.ts_self_tiles), o_tsr = b.add(h.ts_remote_tiles),
                o_segs = b.add(h.segs), o_mv = b.add(sf->h_move_tiles), o_mask = b.add(h.mask),
                o_prr = b.add(h.pr_root), o_prl = b.add(h.pr_leaf), o_mro = b.add(h.m_root), o_mpt = b.add(h.m_ptr),
-               o_mle = b.add(h.m_leaf), o_blk = b.add(h.blocks), o_cmb = b.add(h.combs),
+               o_mle = b.add(h.m_leaf), o_blk = b.add(h.block_recs), o_cmb = b.add(h.combs),
                o_rf = b.add(h.rm_fold_tiles), o_rw = b.add(h.rm_winner_tiles),
                o_rfe = b.add(h.rm_fetch_tiles);
   const size_t bytes = std::max<size_t>(b.host.size(), 256);
@@ -332,7 +332,7 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.m_root = reinterpret_cast<const int32_t *>(base + o_mro);
   d.m_ptr = reinterpret_cast<const int32_t *>(base + o_mpt);
   d.m_leaf = reinterpret_cast<const int32_t *>(base + o_mle);
-  d.blocks = reinterpret_cast<const Block *>(base + o_blk);
+  d.blocks = reinterpret_cast<const BlockRec *>(base + o_blk);
   d.combs = reinterpret_cast<const Comb *>(base + o_cmb);
   d.rm_fold_tiles = reinterpret_cast<const RmTile *>(base + o_rf);
   d.rm_winner_tiles = reinterpret_cast<const RmTile *>(base + o_rw);

@@ -32,7 +32,8 @@ struct HostPlan {
   std::vector<uint32_t> mask;
   std::vector<int32_t> pr_root, pr_leaf;
   std::vector<int32_t> m_root, m_ptr, m_leaf;
-  std::vector<Block> blocks;
+  std::vector<Block> blocks;         // host view (tiling, statistics)
+  std::vector<BlockRec> block_recs;  // device form, one sentinel record at the end
   std::vector<Comb> combs;
   std::vector<RmTile> rm_fold_tiles, rm_winner_tiles, rm_fetch_tiles;
   int32_t n_partial_slots = 0, n_counters = 0;

@@ -443,7 +443,7 @@ struct RmArgs {
   const uint32_t *mask;
   const int32_t *pr_root, *pr_leaf;
   const int32_t *m_root, *m_ptr, *m_leaf;
-  const Block *blocks;
+  const BlockRec *blocks;
   const Comb *combs;
   const RmTile *tiles;
   int32_t ntiles;
@@ -454,6 +454,23 @@ struct RmArgs {
   int32_t *counter;     // scratch: arrivals per (multi-block root, vector); zero between calls
   int32_t nv;
 };
+
+// Expand stored block c (8-byte record plus the next record's first edge) into a Block.
+__device__ __forceinline__ Block load_block(const BlockRec *recs, const Comb *combs, int32_t c) {
+  const BlockRec r = recs[c];
+  const int32_t e1 = recs[c + 1].e0;
+  Block b;
+  b.e0 = r.e0;
+  b.n = e1 - r.e0;
+  if (r.who >= 0) {
+    b.root = r.who;
+    b.comb = -1;
+  } else {
+    b.comb = -r.who - 1;
+    b.root = combs[b.comb].root;
+  }
+  return b;
+}
 
 // Deterministic fold D over n partials (stride nv) of one (root, vector), in place, L2 only.
 template <typename A, int VB, int OP>
@@ -583,49 +600,51 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
   }
 }
 
-// Two single-block roots folded together (Reduce SUM/MIN/MAX): both descriptors, then U + U
-// leaf indices, then U + U leaf values are in flight at once, so each thread keeps two
-// independent load chains going.
-template <typename T, int VB, int OP>
-__device__ __forceinline__ void fold_pair(void *root, void *leaf, const int32_t *m_leaf, int32_t nv, const Block b0,
-                                          const Block b1, int32_t v0, int32_t v1) {
+// NB single-block roots folded together (Reduce SUM/MIN/MAX): NB descriptors, then U leaf
+// indices per root, then U leaf values per root are in flight at once, so each thread keeps NB
+// independent load chains going; each root still folds its leaves in canonical order.
+template <typename T, int VB, int OP, int NB>
+__device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t *m_leaf, int32_t nv,
+                                          const Block (&b)[NB], const int32_t (&v)[NB]) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
   constexpr int U = VB >= 16 ? 1 : 2;
-  const int64_t ri0 = int64_t(b0.root) * nv + v0, ri1 = int64_t(b1.root) * nv + v1;
-  const Pack<T, VB> x0 = ld<T, VB>(root, ri0), x1 = ld<T, VB>(root, ri1);
-  Pack<A, AVB> acc0, acc1;
-  const int32_t nmax = b0.n > b1.n ? b0.n : b1.n;
+  Pack<T, VB> x[NB];
+  Pack<A, AVB> acc[NB];
+  int32_t nmax = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    x[j] = ld<T, VB>(root, int64_t(b[j].root) * nv + v[j]);
+    nmax = b[j].n > nmax ? b[j].n : nmax;
+  }
   for (int32_t e = 0; e < nmax; e += U) {
-    int64_t l0[U], l1[U];
+    int32_t li[NB][U];   // leaf units (< 2^31); -1 past the block's end
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      l0[u] = e + u < b0.n ? int64_t(__ldg(m_leaf + b0.e0 + e + u)) * nv + v0 : -1;
-      l1[u] = e + u < b1.n ? int64_t(__ldg(m_leaf + b1.e0 + e + u)) * nv + v1 : -1;
-    }
-    Pack<T, VB> y0[U], y1[U];
+    for (int j = 0; j < NB; ++j)
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (l0[u] >= 0) y0[u] = ld<T, VB>(leaf, l0[u]);
-      if (l1[u] >= 0) y1[u] = ld<T, VB>(leaf, l1[u]);
-    }
+      for (int u = 0; u < U; ++u) li[j][u] = e + u < b[j].n ? __ldg(m_leaf + b[j].e0 + e + u) : -1;
+    Pack<T, VB> y[NB][U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
+    for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int l = 0; l < Pack<T, VB>::L; ++l) {
-        if (l0[u] >= 0) acc0.v[l] = (e + u == 0) ? to_acc<A, T>(y0[u].v[l]) : combine<OP, A>(acc0.v[l], to_acc<A, T>(y0[u].v[l]));
-        if (l1[u] >= 0) acc1.v[l] = (e + u == 0) ? to_acc<A, T>(y1[u].v[l]) : combine<OP, A>(acc1.v[l], to_acc<A, T>(y1[u].v[l]));
-      }
-    }
+      for (int u = 0; u < U; ++u)
+        if (li[j][u] >= 0) y[j][u] = ld<T, VB>(leaf, int64_t(li[j][u]) * nv + v[j]);
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (li[j][u] >= 0)
+#pragma unroll
+          for (int l = 0; l < Pack<T, VB>::L; ++l)
+            acc[j].v[l] = (e + u == 0) ? to_acc<A, T>(y[j][u].v[l]) : combine<OP, A>(acc[j].v[l], to_acc<A, T>(y[j][u].v[l]));
   }
-  Pack<T, VB> r0 = x0, r1 = x1;
 #pragma unroll
-  for (int l = 0; l < Pack<T, VB>::L; ++l) {
-    r0.v[l] = apply_acc<OP, T, A>(x0.v[l], acc0.v[l]);
-    r1.v[l] = apply_acc<OP, T, A>(x1.v[l], acc1.v[l]);
+  for (int j = 0; j < NB; ++j) {
+    Pack<T, VB> r = x[j];
+#pragma unroll
+    for (int l = 0; l < Pack<T, VB>::L; ++l) r.v[l] = apply_acc<OP, T, A>(x[j].v[l], acc[j].v[l]);
+    st<T, VB>(root, int64_t(b[j].root) * nv + v[j], r);
   }
-  st<T, VB>(root, ri0, r0);
-  st<T, VB>(root, ri1, r1);
 }
 
 template <typename T, int VB, int OP, int MODE>
@@ -737,23 +756,33 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   } else if (t.kind == T_CHUNKS) {
     int32_t w = threadIdx.x;
     if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
-      // pairs of work items: w and w + kThreads
-      for (; w + kThreads < work; w += 2 * kThreads) {
-        const int32_t c0 = nv == 1 ? w : w / nv, v0 = w - c0 * nv;
-        const int32_t w1 = w + kThreads, c1 = nv == 1 ? w1 : w1 / nv, v1 = w1 - c1 * nv;
-        const Block b0 = a.blocks[t.a + c0], b1 = a.blocks[t.a + c1];
-        if (b0.comb < 0 && b1.comb < 0) {
-          fold_pair<T, VB, OP>(a.root, a.leaf, a.m_leaf, nv, b0, b1, v0, v1);
+      // NB work items per thread (w, w + kThreads, ...), folded together when all are
+      // single-block roots
+      constexpr int NB = VB >= 16 ? 2 : 4;
+      for (; w + (NB - 1) * kThreads < work; w += NB * kThreads) {
+        Block b[NB];
+        int32_t v[NB];
+        bool simple = true;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const int32_t wj = w + j * kThreads, cj = nv == 1 ? wj : wj / nv;
+          v[j] = wj - cj * nv;
+          b[j] = load_block(a.blocks, a.combs, t.a + cj);
+          simple &= b[j].comb < 0;
+        }
+        if (simple) {
+          fold_many<T, VB, OP, NB>(a.root, a.leaf, a.m_leaf, nv, b, v);
         } else {
-          fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b0, v0);
-          fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b1, v1);
+#pragma unroll
+          for (int j = 0; j < NB; ++j)
+            fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b[j], v[j]);
         }
       }
     }
     for (; w < work; w += kThreads) {
       const int32_t cl = nv == 1 ? w : w / nv, v = w - cl * nv;
       fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv,
-                                  a.blocks[t.a + cl], v);
+                                  load_block(a.blocks, a.combs, t.a + cl), v);
     }
   }
 }
@@ -773,7 +802,7 @@ struct MaxlocArgs {
   const uint32_t *mask;
   const int32_t *pr_root, *pr_leaf;
   const int32_t *m_leaf;
-  const Block *blocks;
+  const BlockRec *blocks;
   const Comb *combs;
   const RmTile *tiles;
   void *out;            // max values, units of bs elements
@@ -816,7 +845,7 @@ __global__ void __launch_bounds__(kThreads) maxloc_kernel(MaxlocArgs a) {
   } else if (t.kind == T_CHUNKS) {
     for (int32_t w = threadIdx.x; w < work; w += kThreads) {
       const int32_t cl = w / bs, c = w - cl * bs;
-      const Block b = a.blocks[t.a + cl];
+      const Block b = load_block(a.blocks, a.combs, t.a + cl);
       int32_t best_l = a.m_leaf[b.e0];
       T best = leaf[int64_t(best_l) * bs + c];
       for (int32_t e = 1; e < b.n; ++e) {

@@ -97,6 +97,15 @@ struct Comb {
   int32_t ctr;      // counter index
   int32_t nch;      // number of blocks
   int32_t e_first;  // first edge of the root in m_leaf
+  int32_t root;     // root unit
+};
+
+// A fold block as stored: 8 bytes.  who >= 0 is the root unit of a single-block root,
+// who < 0 is -(Comb index + 1); the block's leaf count is the next record's e0 minus its own
+// (blocks are stored in m_leaf order, with one sentinel record after the last).
+struct BlockRec {
+  int32_t who;
+  int32_t e0;
 };
 
 struct SegCopy {                 // one (root rank -> leaf rank) chunk of the buffer move
@@ -117,7 +126,7 @@ struct DevPlan {
   const uint32_t *mask;
   const int32_t *pr_root, *pr_leaf;
   const int32_t *m_root, *m_ptr, *m_leaf;   // multi roots: root unit, CSR pointers, leaf units
-  const Block *blocks;                      // fold blocks of multi roots
+  const BlockRec *blocks;                   // fold blocks of multi roots (+ sentinel)
   const Comb *combs;                        // multi roots with several blocks
   const RmTile *rm_fold_tiles;              // masked + pairs + chunks
   const RmTile *rm_winner_tiles;            // masked + pairs + winners

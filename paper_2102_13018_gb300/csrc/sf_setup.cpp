@@ -394,17 +394,19 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       int32_t comb = -1;
       if (nch > 1) {
         comb = int32_t(plan.combs.size());
-        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_counters, nch, plan.m_ptr[m]});
+        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_counters, nch, plan.m_ptr[m], plan.m_root[m]});
         plan.n_partial_slots += nch;
         plan.n_counters++;
       }
       for (int32_t c = 0; c < nch; ++c) {
         const int32_t e0 = plan.m_ptr[m] + c * FOLD_BLOCK;
         plan.blocks.push_back(Block{plan.m_root[m], e0, std::min(FOLD_BLOCK, plan.m_ptr[m + 1] - e0), comb});
+        plan.block_recs.push_back(BlockRec{comb < 0 ? plan.m_root[m] : -(comb + 1), e0});
         blk_m.push_back(m);
       }
       heavy[m] = nch >= 16;
     }
+    plan.block_recs.push_back(BlockRec{0, int32_t(plan.m_leaf.size())});   // sentinel
     // tiles, ordered by the first root they touch (heavy multi roots first)
     struct Keyed { int64_t key; RmTile t; };
     std::vector<Keyed> common;
