@@ -472,23 +472,36 @@ __device__ __forceinline__ Block load_block(const BlockRec *recs, const Comb *co
   return b;
 }
 
+// Left fold of n partials (stride nv) starting at slot, 8 loads in flight, L2 only.
+template <typename A, int VB, int OP>
+__device__ Pack<A, VB> fold_range(const void *partial, int64_t slot, int32_t nv, int32_t v, int32_t n) {
+  constexpr int U = 8;
+  Pack<A, VB> acc = ld_cg<A, VB>(partial, slot * nv + v);
+  int32_t i = 1;
+  for (; i + U <= n; i += U) {
+    Pack<A, VB> y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) y[u] = ld_cg<A, VB>(partial, (slot + i + u) * nv + v);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = combine<OP, A, VB>(acc, y[u]);
+  }
+  for (; i < n; ++i) acc = combine<OP, A, VB>(acc, ld_cg<A, VB>(partial, (slot + i) * nv + v));
+  return acc;
+}
+
 // Deterministic fold D over n partials (stride nv) of one (root, vector), in place, L2 only.
 template <typename A, int VB, int OP>
 __device__ Pack<A, VB> fold_partials(void *partial, int64_t slot, int32_t nv, int32_t v, int32_t n) {
   while (n > FOLD_BLOCK) {
     int32_t m = 0;
     for (int32_t s = 0; s < n; s += FOLD_BLOCK) {
-      const int32_t e = min(s + FOLD_BLOCK, n);
-      Pack<A, VB> acc = ld_cg<A, VB>(partial, (slot + s) * nv + v);
-      for (int32_t i = s + 1; i < e; ++i) acc = combine<OP, A, VB>(acc, ld_cg<A, VB>(partial, (slot + i) * nv + v));
+      const Pack<A, VB> acc = fold_range<A, VB, OP>(partial, slot + s, nv, v, min(FOLD_BLOCK, n - s));
       st_cg<A, VB>(partial, (slot + m) * nv + v, acc);   // m <= s: its block was already read
       ++m;
     }
     n = m;
   }
-  Pack<A, VB> acc = ld_cg<A, VB>(partial, slot * nv + v);
-  for (int32_t i = 1; i < n; ++i) acc = combine<OP, A, VB>(acc, ld_cg<A, VB>(partial, (slot + i) * nv + v));
-  return acc;
+  return fold_range<A, VB, OP>(partial, slot, nv, v, n);
 }
 
 // One single-leaf edge (root unit ru, leaf unit lu), vector v, all loads issued by the caller.
@@ -580,16 +593,32 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
     bool finish = b.comb < 0;
     if (!finish) {
       const Comb cb = combs[b.comb];
-      const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;
+      const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;       // block index in the root
+      const int32_t sb = ci / FOLD_BLOCK;                         // super-block
+      const int32_t nsb = (cb.nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
+      const int32_t in_sb = min(FOLD_BLOCK, cb.nch - sb * FOLD_BLOCK);
       st_cg<A, AVB>(partial, (int64_t(cb.slot) + ci) * nv + v, acc);
       __threadfence();
-      int32_t *ctr = counter + int64_t(cb.ctr) * nv + v;
-      if (atomicAdd(ctr, 1) == cb.nch - 1) {
+      int32_t *ctr = counter + int64_t(cb.ctr + sb) * nv + v;
+      if (atomicAdd(ctr, 1) == in_sb - 1) {
+        // last block of its super-block: left fold of the super-block's partials
         __threadfence();
-        acc = fold_partials<A, AVB, OP>(partial, cb.slot, nv, v, cb.nch);
+        acc = fold_range<A, AVB, OP>(partial, int64_t(cb.slot) + sb * FOLD_BLOCK, nv, v, in_sb);
         *ctr = 0;   // ready for the next operation
-        finish = true;
-        xr = ld<T, VB>(root, ri);
+        if (nsb == 1) {
+          finish = true;
+        } else {
+          st_cg<A, AVB>(partial, (int64_t(cb.slot1) + sb) * nv + v, acc);
+          __threadfence();
+          int32_t *rctr = counter + int64_t(cb.ctr + nsb) * nv + v;
+          if (atomicAdd(rctr, 1) == nsb - 1) {
+            __threadfence();
+            acc = fold_partials<A, AVB, OP>(partial, cb.slot1, nv, v, nsb);
+            *rctr = 0;
+            finish = true;
+          }
+        }
+        if (finish) xr = ld<T, VB>(root, ri);
       }
     }
     if (finish) {

@@ -92,9 +92,13 @@ struct Block {
 };
 
 // A root with several fold blocks: where its block partials and arrival counter live.
+// Blocks are folded in two levels, the way D is defined: the partials of each run of
+// FOLD_BLOCK consecutive blocks (a super-block) are folded by the super-block's last arriving
+// block, and the super-block results by the last arriving super-block.
 struct Comb {
-  int32_t slot;     // first partial slot
-  int32_t ctr;      // counter index
+  int32_t slot;     // first level-0 partial slot (one per block)
+  int32_t slot1;    // first level-1 partial slot (one per super-block)
+  int32_t ctr;      // first counter: one per super-block, then one for the root
   int32_t nch;      // number of blocks
   int32_t e_first;  // first edge of the root in m_leaf
   int32_t root;     // root unit

@@ -394,9 +394,11 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       int32_t comb = -1;
       if (nch > 1) {
         comb = int32_t(plan.combs.size());
-        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_counters, nch, plan.m_ptr[m], plan.m_root[m]});
-        plan.n_partial_slots += nch;
-        plan.n_counters++;
+        const int32_t nsuper = (nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
+        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_partial_slots + nch, plan.n_counters, nch,
+                                  plan.m_ptr[m], plan.m_root[m]});
+        plan.n_partial_slots += nch + nsuper;
+        plan.n_counters += nsuper + 1;
       }
       for (int32_t c = 0; c < nch; ++c) {
         const int32_t e0 = plan.m_ptr[m] + c * FOLD_BLOCK;
