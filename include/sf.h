@@ -205,6 +205,18 @@ int sf_reduce_with_memtype_end(sf_t *sf, sf_unit unit, int32_t leafmtype, const 
 int sf_create_embedded_root_sf(const sf_t *sf, int64_t n, const int64_t selected_roots[], sf_t **out);
 int sf_create_embedded_leaf_sf(const sf_t *sf, int64_t n, const int64_t selected_leaves[], sf_t **out);
 
+/* Composition (PetscSFCompose): A's leaf space is B's root space (leafoff of A equals rootoff
+ * of B rank by rank).  AB has A's roots and B's leaves; B's leaf l connects to A's root a when
+ * l's root in B is a leaf of A connected to a (a B leaf whose B root is an isolated A leaf is
+ * left out).  Bcast over AB equals Bcast over A then Bcast over B.  New forest in *AB. */
+int sf_compose(const sf_t *A, const sf_t *B, sf_t **AB);
+
+/* Inverse composition (PetscSFComposeInverse): A and B share the leaf space, and every root of
+ * B has at most one leaf (else SF_ERR_ARG).  AB has A's roots, and B's roots are its leaves: B's
+ * root r connects to A's root a when r's leaf is a leaf of A connected to a.  The leaf space of
+ * AB is B's root space.  New forest in *AB. */
+int sf_compose_inverse(const sf_t *A, const sf_t *B, sf_t **AB);
+
 /* Multi-forest (PetscSFGetMultiSF): every root of degree d becomes d roots, and the k-th leaf of
  * a root in canonical order connects to its k-th new root.  Built on first use with the
  * paper's recipe -- Reduce SUM of ones for the degrees, roots set to their rank's degree prefix

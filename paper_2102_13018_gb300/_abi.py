@@ -98,6 +98,8 @@ def load():
     lib.sf_create_embedded_root_sf.argtypes = [vp, i64, P(i64), P(vp)]
     lib.sf_create_embedded_leaf_sf.argtypes = [vp, i64, P(i64), P(vp)]
     lib.sf_get_multi_sf.argtypes = [vp, vp, P(vp)]
+    lib.sf_compose.argtypes = [vp, vp, P(vp)]
+    lib.sf_compose_inverse.argtypes = [vp, vp, P(vp)]
     for name in ("sf_gather_begin", "sf_gather_end", "sf_scatter_begin", "sf_scatter_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, vp, vp, vp]
     lib.sf_maxloc_scatter.argtypes = [vp, sf_unit, vp, vp, vp, vp]

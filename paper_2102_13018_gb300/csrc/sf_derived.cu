@@ -1,4 +1,6 @@
-// sf_derived.cu -- forests derived from a forest (Sec. III.B-C):
+// sf_derived.cu -- forests derived from forests (Sec. III.B-C):
+//  * composition: AB connects A's roots to B's leaves through A's leaves = B's roots; the
+//    inverse composition connects A's roots to B's roots through their shared leaves;
 //  * embedded root / leaf forests: the edges of selected roots or leaves only, with the same
 //    root and leaf numbering, so the original data buffers serve the new forest;
 //  * the multi-forest: every root split into as many roots as it has leaves, leaf i of a root
@@ -139,9 +141,90 @@ int build_multi(sf_t *sf, cudaStream_t s, sf_t **out) {
   return SF_SUCCESS;
 }
 
+// AB from per-rank leaf lists: leaves[q] = (local index, root rank, root index), layout of the
+// leaf space given by extents, roots by nroots.
+int from_edges(int32_t P, const std::vector<int64_t> &nroots, const std::vector<int64_t> &extents,
+               const std::vector<std::vector<std::pair<int64_t, sf_node>>> &leaves, sf_t **out) {
+  std::vector<int64_t> nleaves(P);
+  std::vector<std::vector<int64_t>> il(P);
+  std::vector<std::vector<sf_node>> ir(P);
+  for (int32_t q = 0; q < P; ++q) {
+    nleaves[q] = int64_t(leaves[q].size());
+    for (const auto &lv : leaves[q]) {
+      il[q].push_back(lv.first);
+      ir[q].push_back(lv.second);
+    }
+  }
+  std::vector<const int64_t *> ilp(P);
+  std::vector<const sf_node *> irp(P);
+  for (int32_t q = 0; q < P; ++q) {
+    ilp[q] = il[q].empty() ? nullptr : il[q].data();
+    irp[q] = ir[q].empty() ? nullptr : ir[q].data();
+  }
+  sf_t *n = new (std::nothrow) sf_t();
+  if (!n) return SF_ERR_ALLOC;
+  const int rc = build_graph_extents(P, nroots.data(), nleaves.data(), ilp.data(), irp.data(), extents.data(), n->g);
+  if (rc) {
+    delete n;
+    return rc;
+  }
+  n->info.nranks = P;
+  *out = n;
+  return SF_SUCCESS;
+}
+
+// root of the edge leaving global leaf unit l of `g`, or {-1, -1} when l is isolated
+std::vector<sf_node> leaf_to_root(const Graph &g) {
+  std::vector<sf_node> m(g.leafoff[g.P], sf_node{-1, -1});
+  for (int32_t q = 0; q < g.P; ++q)
+    for (int64_t i = 0, e = g.edgeoff[q]; e < g.edgeoff[q + 1]; ++i, ++e)
+      m[g.leafoff[q] + (g.has_ilocal[q] ? g.ilocal[e] : i)] = sf_node{g.rrank[e], g.rindex[e]};
+  return m;
+}
+
 }  // namespace
 
 extern "C" {
+
+int sf_compose(const sf_t *A, const sf_t *B, sf_t **AB) {
+  if (!A || !B || !AB) return SF_ERR_NULL;
+  const Graph &a = A->g, &b = B->g;
+  if (a.P != b.P) return SF_ERR_ARG;
+  for (int32_t p = 0; p < a.P; ++p)   // A's leaf space is B's root space
+    if (a.leafoff[p + 1] - a.leafoff[p] != b.nroots[p]) return SF_ERR_ARG;
+  const std::vector<sf_node> aroot = leaf_to_root(a);
+  std::vector<std::vector<std::pair<int64_t, sf_node>>> leaves(b.P);
+  std::vector<int64_t> extents(b.P);
+  for (int32_t q = 0; q < b.P; ++q) {
+    extents[q] = b.leafoff[q + 1] - b.leafoff[q];
+    for (int64_t i = 0, e = b.edgeoff[q]; e < b.edgeoff[q + 1]; ++i, ++e) {
+      const sf_node r = aroot[a.leafoff[b.rrank[e]] + b.rindex[e]];   // B's root = A's leaf
+      if (r.rank >= 0) leaves[q].push_back({b.has_ilocal[q] ? b.ilocal[e] : i, r});
+    }
+  }
+  return from_edges(a.P, a.nroots, extents, leaves, AB);
+}
+
+int sf_compose_inverse(const sf_t *A, const sf_t *B, sf_t **AB) {
+  if (!A || !B || !AB) return SF_ERR_NULL;
+  const Graph &a = A->g, &b = B->g;
+  if (a.P != b.P) return SF_ERR_ARG;
+  for (int32_t p = 0; p <= a.P; ++p)   // A and B share the leaf space
+    if (a.leafoff[p] != b.leafoff[p]) return SF_ERR_ARG;
+  const std::vector<sf_node> aroot = leaf_to_root(a);
+  std::vector<uint8_t> seen(b.rootoff[b.P], 0);
+  std::vector<std::vector<std::pair<int64_t, sf_node>>> leaves(b.P);
+  for (int32_t q = 0; q < b.P; ++q)
+    for (int64_t i = 0, e = b.edgeoff[q]; e < b.edgeoff[q + 1]; ++i, ++e) {
+      const int64_t broot = b.rootoff[b.rrank[e]] + b.rindex[e];
+      if (seen[broot]++) return SF_ERR_ARG;   // B's roots must have degree at most one
+      const sf_node r = aroot[b.leafoff[q] + (b.has_ilocal[q] ? b.ilocal[e] : i)];
+      if (r.rank >= 0) leaves[b.rrank[e]].push_back({b.rindex[e], r});   // leaf = B's root
+    }
+  for (auto &l : leaves) std::sort(l.begin(), l.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+  return from_edges(a.P, a.nroots, b.nroots, leaves, AB);
+}
+
 
 int sf_create_embedded_root_sf(const sf_t *sf, int64_t n, const int64_t selected_roots[], sf_t **out) {
   if (!sf || !out || (n > 0 && !selected_roots)) return SF_ERR_NULL;

@@ -184,6 +184,18 @@ class StarForest:
                                                    ctypes.byref(h)), "sf_create_embedded_leaf_sf")
         return StarForest._wrap(h)
 
+    def compose(self, other: "StarForest") -> "StarForest":
+        """AB: this forest's roots to other's leaves (this forest's leaves = other's roots)."""
+        h = ctypes.c_void_p()
+        check(self._lib.sf_compose(self._h, other._h, ctypes.byref(h)), "sf_compose")
+        return StarForest._wrap(h)
+
+    def compose_inverse(self, other: "StarForest") -> "StarForest":
+        """AB: this forest's roots to other's roots through the shared leaves."""
+        h = ctypes.c_void_p()
+        check(self._lib.sf_compose_inverse(self._h, other._h, ctypes.byref(h)), "sf_compose_inverse")
+        return StarForest._wrap(h)
+
     def multi_sf(self, stream=None) -> "StarForest":
         """The multi-forest (owned by this forest)."""
         h = ctypes.c_void_p()

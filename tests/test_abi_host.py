@@ -175,3 +175,22 @@ def test_embedded_root_and_leaf_forests_keep_the_layout():
         sf.embedded_roots([9])
     assert e.value.name == "SF_ERR_RANGE"
     assert sf.embedded_roots([]).analyze().info()["nedges"] == 0
+
+
+def test_compose_checks_layouts_and_degrees():
+    a = StarForest.from_forest(sfgen.fig2())          # leaf extents 4, 4, 3
+    with pytest.raises(SFError) as e:
+        a.compose(a)                                   # A's leaf space (4,4,3) is not A's roots (3,4,2)
+    assert e.value.name == "SF_ERR_ARG"
+    with pytest.raises(SFError) as e:
+        a.compose_inverse(a)                           # shared leaves, but A's root (1,0) has 3 leaves
+    assert e.value.name == "SF_ERR_ARG"
+    # B with roots = A's leaf space: rank q owns extent(q) roots, one leaf per root, identity
+    ext = [4, 4, 3]
+    b = sfgen.Forest(3, np.array(ext), np.array(ext), [None] * 3,
+                     [np.full(n, q, np.int32) for q, n in enumerate(ext)],
+                     [np.arange(n, dtype=np.int64) for n in ext])
+    ab = a.compose(StarForest.from_forest(b))
+    info = ab.analyze().info()
+    assert info["nedges"] == 10                       # rank 1's isolated leaf 2 drops out
+    assert ab.rootoff.tolist() == a.rootoff.tolist()

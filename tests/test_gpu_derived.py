@@ -91,3 +91,61 @@ def test_embedded_root_forest_moves_only_selected_roots(f):
     got = to_host(r, "fp64")
     unsel = np.setdiff1d(np.arange(sf.nroots_total), sel)
     assert np.array_equal(got[unsel], root[unsel])
+
+
+def _roots_for_leaf_space(seed, ext):
+    """A forest whose rank q owns ext[q] roots (a leaf space) and whose leaves point at them."""
+    nl = [int(x) + 3 for x in ext]
+    total = int(np.sum(ext))
+    off = np.concatenate([[0], np.cumsum(ext)])
+    rr, ri = [], []
+    for q, n in enumerate(nl):
+        g = sfgen.rng.randint(seed, 50 + q, n, 0, total)
+        r = np.searchsorted(off, g, side="right") - 1
+        rr.append(r.astype(np.int32))
+        ri.append((g - off[r]).astype(np.int64))
+    return sfgen.Forest(len(ext), np.array(ext), np.array(nl), [None] * len(ext), rr, ri, name=f"onleaves{seed}")
+
+
+def test_compose_equals_two_bcasts():
+    a = sfgen.random_forest(71, 4, 200, 250, sparse=True)
+    sfa = StarForest.from_forest(a)
+    ext = np.diff(sfa.leafoff)
+    b = _roots_for_leaf_space(72, ext)
+    ab = sfa.compose(StarForest.from_forest(b)).setup()
+    x, _ = make_data(a, "fp64", 2, 1600)
+    mid0 = np.full(int(sfa.leafoff[-1]) * 2, -5.0)
+    mid = oracle.bcast(a, "fp64", 2, x, mid0, "REPLACE")
+    rob, lob = oracle.layout(b)
+    out0 = np.full(int(lob[-1]) * 2, 7.0)
+    two_step = oracle.bcast(b, "fp64", 2, mid, out0, "REPLACE")
+    got = to_dev(out0, "fp64")
+    ab.bcast(to_dev(x, "fp64"), got, "REPLACE", bs=2)
+    # B leaves whose B root is an isolated A leaf are not in AB: the two-step result shows -5
+    g = to_host(got, "fp64").reshape(-1, 2)
+    w = two_step.reshape(-1, 2)
+    through = w[:, 0] != -5.0
+    assert np.array_equal(g[through], w[through])
+    assert np.all(g[~through] == 7.0)
+
+
+def test_compose_inverse_equals_bcast_then_reduce_replace():
+    a = sfgen.random_forest(73, 3, 150, 200, sparse=False)
+    sfa = StarForest.from_forest(a)
+    ext = np.diff(sfa.leafoff)
+    NL = int(ext.sum())
+    perm = np.argsort(sfgen.rng.u64(74, 1, NL), kind="stable")     # bijection leaves <-> roots
+    lo = np.concatenate([[0], np.cumsum(ext)])
+    rr = [(np.searchsorted(lo, perm[lo[q]:lo[q + 1]], side="right") - 1).astype(np.int32) for q in range(3)]
+    ri = [(perm[lo[q]:lo[q + 1]] - lo[rr[q]]).astype(np.int64) for q in range(3)]
+    b = sfgen.Forest(3, ext, ext, [None] * 3, rr, ri, name="bijection")
+    ab = sfa.compose_inverse(StarForest.from_forest(b)).setup()
+    x, _ = make_data(a, "fp64", 1, 1700)
+    mid = oracle.bcast(a, "fp64", 1, x, np.full(NL, -5.0), "REPLACE")
+    want = oracle.reduce(b, "fp64", 1, mid, np.full(NL, 9.0), "REPLACE")
+    got = to_dev(np.full(NL, 9.0), "fp64")
+    ab.bcast(to_dev(x, "fp64"), got, "REPLACE")
+    g = to_host(got, "fp64")
+    through = want != -5.0
+    assert np.array_equal(g[through], want[through])
+    assert np.all(g[~through] == 9.0)
