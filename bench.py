@@ -33,7 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SF Bcast/Reduce effective HBM GB/s (% of peak); batched vs per-SF launch time"
-KERNEL_SOURCES = ["paper_2102_13018_gb300/csrc/sf_kernels.cuh"]
+# the kernels and the plan layout they read: DRAM traffic from a capture holds while these are unchanged
+KERNEL_SOURCES = ["paper_2102_13018_gb300/csrc/sf_kernels.cuh", "paper_2102_13018_gb300/csrc/sf_plan.h",
+                  "paper_2102_13018_gb300/csrc/sf_setup.cpp"]
 
 
 def parse():
@@ -49,6 +51,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pingpong", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "halo", "autograd"],
+                    help="run one extra section alone (halo exchange or autograd) and print it")
     ap.add_argument("--batch-forests", type=int, default=512)
     return ap.parse_args()
 
@@ -325,6 +330,102 @@ def run_pingpong(stream):
             "sizes": out}
 
 
+def run_autograd(flush):
+    """Differentiable message passing on the power-law graph (2^20 roots, 2^23 leaves, bs = 64):
+    forward Bcast then backward (Reduce SUM of the leaf gradient) through the library's
+    autograd functions, against the same computation written with plain PyTorch ops
+    (index_select forward, index_add_ backward -- atomic, not reproducible)."""
+    import numpy as np
+    import torch
+    import sfgen
+    from paper_2102_13018_gb300 import StarForest
+    from paper_2102_13018_gb300 import autograd as sfa
+    f = sfgen.cfg5_powerlaw()
+    sf = StarForest.from_forest(f).setup().set_mode("deterministic")
+    per = int(f.nroots[0])
+    idx = torch.from_numpy(np.concatenate([f.iremote_rank[q].astype(np.int64) * per + f.iremote_index[q]
+                                           for q in range(f.nranks)])).cuda()
+    info = sf.info()
+    out = {}
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        x = torch.rand(sf.nroots_total, 64, device="cuda").to(dt).requires_grad_(True)
+        g = torch.rand(sf.leaf_extent, 64, device="cuda").to(dt)
+        ub = 64 * x.element_size()
+        fwd_bytes = ub * info["connected_roots"] + ub * info["nedges"] + 4 * info["nedges"]
+        bwd_bytes = ub * info["nedges"] + 2 * ub * info["connected_roots"] + 4 * info["nedges"]
+
+        def ours():
+            x.grad = None
+            sfa.bcast(sf, x).backward(g)
+
+        def plain():
+            x.grad = None
+            torch.index_select(x, 0, idx).backward(g)
+
+        res = {}
+        for label, fn in (("sf_autograd", ours), ("torch_index_select_add", plain)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(10):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            res[label] = {"ms": ms, "gbs": (fwd_bytes + bwd_bytes) / (ms * 1e-3) / 1e9}
+        out[name] = res
+    return {"workload": "power-law message passing: 2^20 roots, 2^23 leaves (Chung-Lu, exponent 2.2), "
+                        "bs=64; forward Bcast + backward Reduce SUM", **out}
+
+
+def run_halo(flush, peak):
+    """3-D halo exchange, 256^3 fp64 grid in 4x4x4 ranks, 27-point ghosts (about 1.2M ghost
+    leaves): Bcast REPLACE (ghost update) and Reduce SUM (ghost accumulate) at bs = 1 and 5.
+    Each call is timed alone with CUDA events after an L2 flush; bytes are algorithmic (roots
+    read once, leaves written / read once, roots read and written for Reduce)."""
+    import torch
+    import sfgen
+    from paper_2102_13018_gb300 import StarForest
+    f = sfgen.cfg2_halo()
+    sf = StarForest.from_forest(f).setup()
+    info = sf.info()
+    out = {"workload": "halo_27pt: 256^3 fp64 grid, 4x4x4 simulated ranks, width-1 ghost layers",
+           "ghost_leaves": info["nedges"], "pattern_edges": info["edges_both_pattern"],
+           "ts_tile_edges": info["ts_tile_edges"], "rm_tile_edges": info["rm_tile_edges"]}
+    for bs in (1, 5):
+        x = torch.rand(sf.nroots_total * bs, dtype=torch.float64, device="cuda")
+        lv = torch.zeros(sf.leaf_extent * bs, dtype=torch.float64, device="cuda")
+        ub = 8 * bs
+        for label, mode, nbytes in (
+                ("bcast_replace", None, ub * info["connected_roots"] + ub * info["nedges"]),
+                ("reduce_sum_atomic", "atomic", ub * info["nedges"] + 2 * ub * info["connected_roots"]),
+                ("reduce_sum_deterministic", "deterministic", ub * info["nedges"] + 2 * ub * info["connected_roots"])):
+            if mode:
+                sf.set_mode(mode)
+                fn = lambda: sf.reduce(lv, x, "SUM", bs=bs)    # noqa: E731
+            else:
+                fn = lambda: sf.bcast(x, lv, "REPLACE", bs=bs)  # noqa: E731
+            ev = []
+            for i in range(33):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                if i >= 3:
+                    ev.append((e0, e1))
+            torch.cuda.synchronize()
+            us = statistics.median(a.elapsed_time(b) for a, b in ev) * 1e3
+            gbs = nbytes / (us * 1e-6) / 1e9
+            out[f"{label}_bs{bs}"] = {"us": us, "gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 def max_over_ranks(local_ms: float, world: int, device: str = "cpu") -> float:
     """Slowest rank's timed total (every rank runs an independent replica)."""
     import torch
@@ -366,6 +467,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import sfgen
     from paper_2102_13018_gb300 import StarForest, launch_count
+
+    if args.only != "all":
+        # one extra section alone (for profiling it); prints its own JSON object
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        res = run_halo(flush, measured_peak()[0]) if args.only == "halo" else run_autograd(flush)
+        if rank == 0:
+            print(json.dumps({"section": args.only, **res}))
+        return
 
     forest = build_forest(args)
     t0 = time.perf_counter()
@@ -497,6 +606,11 @@ def main():
     if not args.no_pingpong:
         pingpong = run_pingpong(stream)
 
+    autograd = halo = None
+    if not args.no_extras:
+        autograd = run_autograd(flush)
+        halo = run_halo(flush, peak)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(args, stream, flush)
@@ -517,7 +631,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "ops": ops, "variants": variants, "batched": batched,
-                "pingpong": pingpong,
+                "pingpong": pingpong, "autograd": autograd, "halo": halo,
                 "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
                                               "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
                                               "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}

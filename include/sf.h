@@ -46,7 +46,9 @@ typedef struct {
 /* Element types of a unit. */
 enum { SF_INT32 = 0, SF_INT64 = 1, SF_FP32 = 2, SF_FP64 = 3, SF_BF16 = 4 };
 
-/* A unit: bs consecutive elements of dtype (bs >= 1). */
+/* A unit: bs consecutive elements of dtype, 1 <= bs and bs x element size <= SF_MAX_UNIT_BYTES
+ * (larger units are rejected with SF_ERR_ARG; the kernels index a tile's work in 32 bits). */
+#define SF_MAX_UNIT_BYTES (1 << 19)
 typedef struct {
   int32_t dtype;
   int32_t bs;
@@ -124,6 +126,9 @@ typedef struct {
   int64_t rm_pairs;            /* root-major plan: other single-leaf roots */
   int64_t rm_chunks;           /* root-major plan: blocks of SF_FOLD_BLOCK leaves of multi roots */
   int64_t device_plan_bytes;   /* device memory held by the plans */
+  int64_t ts_tile_edges;       /* edges per tile of a two-sided run (smaller forests: smaller tiles) */
+  int64_t rm_tile_edges;       /* edges per masked / single-leaf tile of the root-major plan */
+  int64_t rm_tile_blocks;      /* fold blocks per chunk tile of the root-major plan (at most) */
 } sf_info;
 
 /* Create a star forest (PetscSFCreate + PetscSFSetGraph, Sec. III.A).
@@ -314,6 +319,16 @@ int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootda
 /* Free the forest and its device plans.  SF_ERR_PENDING (and nothing freed) if a Begin has
  * no End yet.  Synchronises the device work the library enqueued before freeing. */
 int sf_destroy(sf_t *sf);
+
+/* Device status bits of a forest: waits inside the kernels are bounded (about one second);
+ * one that runs out sets its bit, skips its tile and lets the kernel finish. */
+#define SF_DEVSTAT_STAGE_TIMEOUT 1   /* a bulk copy of plan indices into shared memory did not land */
+
+/* The forest's device status bits raised since the previous call (0: none), then cleared.
+ * Synchronises `stream` (the work the library enqueued on it).  A nonzero status means the
+ * results of the operations since the previous call are not to be trusted.
+ * Errors: SF_ERR_NULL, SF_ERR_STATE (no setup), SF_ERR_CUDA. */
+int sf_get_device_status(sf_t *sf, sf_stream_t stream, int32_t *status);
 
 /* Static description of an error code (never NULL). */
 const char *sf_error_string(int code);

@@ -17,6 +17,8 @@ SF_MEM_HOST, SF_MEM_DEVICE = 0, 1
 SF_OP_BCAST, SF_OP_REDUCE, SF_OP_BARRIER = 0, 1, 2
 SF_FOLD_BLOCK = 64
 SF_NOALLOC_SCRATCH_BYTES = 16 << 20
+SF_DEVSTAT_STAGE_TIMEOUT = 1
+SF_MAX_UNIT_BYTES = 1 << 19
 
 ERRORS = {0: "SF_SUCCESS", 1: "SF_ERR_ARG", 2: "SF_ERR_NULL", 3: "SF_ERR_RANGE", 4: "SF_ERR_DUP_LEAF",
           5: "SF_ERR_STATE", 6: "SF_ERR_NO_PENDING", 7: "SF_ERR_PENDING", 8: "SF_ERR_UNSUPPORTED",
@@ -51,7 +53,8 @@ class sf_info(ctypes.Structure):
                    "nroots_total", "leaf_extent_total", "nedges", "max_in_degree", "connected_roots",
                    "multi_roots", "multi_edges", "segments", "self_edges", "runs", "runs_pattern", "runs_3d",
                    "edges_both_pattern", "edges_one_indexed", "edges_two_indexed", "rm_masked_runs",
-                   "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")]
+                   "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes", "ts_tile_edges",
+                   "rm_tile_edges", "rm_tile_blocks")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -95,6 +98,7 @@ def load():
         getattr(lib, name).argtypes = [vp, sf_unit, i32, vp, i32, vp, i32, vp]
     lib.sf_reduce_noalloc.argtypes = [vp, sf_unit, vp, vp, i32, vp]
     lib.sf_reduce_maxloc.argtypes = [vp, sf_unit, vp, vp, vp, vp]
+    lib.sf_get_device_status.argtypes = [vp, vp, P(i32)]
     lib.sf_create_embedded_root_sf.argtypes = [vp, i64, P(i64), P(vp)]
     lib.sf_create_embedded_leaf_sf.argtypes = [vp, i64, P(i64), P(vp)]
     lib.sf_get_multi_sf.argtypes = [vp, vp, P(vp)]

@@ -50,8 +50,10 @@ void release(DevBuf &b) {
 struct BlobBuilder {
   std::vector<char> host;
   template <typename V> size_t add(const std::vector<V> &v) {
+    // 256-byte aligned, and followed by at least 16 bytes of the blob: a bulk copy of a span
+    // widened to 16-byte boundaries stays inside the allocation
     size_t off = (host.size() + 255) & ~size_t(255);
-    host.resize(off + v.size() * sizeof(V));
+    host.resize(off + v.size() * sizeof(V) + 16);
     if (!v.empty()) memcpy(host.data() + off, v.data(), v.size() * sizeof(V));
     return off;
   }
@@ -72,7 +74,7 @@ int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> 
 }
 
 int check_unit(const sf_unit &u, int32_t op) {
-  if (elem_size(u.dtype) == 0 || u.bs < 1 || u.bs > (1 << 20)) return SF_ERR_ARG;
+  if (elem_size(u.dtype) == 0 || u.bs < 1 || int64_t(u.bs) * elem_size(u.dtype) > SF_MAX_UNIT_BYTES) return SF_ERR_ARG;
   if (op < SF_REPLACE || op > SF_MAX) return SF_ERR_ARG;
   return SF_SUCCESS;
 }
@@ -111,6 +113,9 @@ TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *
   a.dst = dst;
   a.upd = upd;
   a.nv = nv;
+  const DivMagic dm = div_magic(uint32_t(nv));
+  a.nv_m = dm.m;
+  a.nv_s = dm.s;
   a.phase = phase;
   return a;
 }
@@ -132,7 +137,11 @@ RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *
   a.upd = upd;
   a.partial = sf->partial.p;
   a.counter = static_cast<int32_t *>(sf->counter.p);
+  a.status = static_cast<int32_t *>(sf->status.p);
   a.nv = nv;
+  const DivMagic dm = div_magic(uint32_t(nv));
+  a.nv_m = dm.m;
+  a.nv_s = dm.s;
   return a;
 }
 
@@ -345,7 +354,7 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.n_counters = h.n_counters;
   // fold scratch for units up to 16 bytes, so common operations allocate nothing later
   if ((rc = ensure(sf->partial, size_t(h.n_partial_slots) * 16, false, s)) ||
-      (rc = ensure(sf->counter, size_t(h.n_counters) * 4 * 8, true, s)))
+      (rc = ensure(sf->counter, size_t(h.n_counters) * 4 * 8, true, s)) || (rc = ensure(sf->status, 16, true, s)))
     return rc;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SF_ERR_CUDA;
   sf->info.device_plan_bytes = int64_t(bytes);
@@ -564,8 +573,26 @@ int sf_destroy(sf_t *sf) {
     release(sf->leafbuf);
     release(sf->stage_root);
     release(sf->stage_leaf);
+    release(sf->status);
   }
   delete sf;
+  return SF_SUCCESS;
+}
+
+static_assert(SF_DEVSTAT_STAGE_TIMEOUT == DEVSTAT_STAGE_TIMEOUT, "status bits agree");
+
+int sf_get_device_status(sf_t *sf, sf_stream_t stream, int32_t *status) {
+  int rc;
+  if ((rc = ensure_ready(sf))) return rc;
+  if (!status) return SF_ERR_NULL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t v = 0;
+  if (cudaMemcpyAsync(&v, sf->status.p, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(sf->status.p, 0, sizeof v, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  *status = v;
   return SF_SUCCESS;
 }
 

@@ -191,11 +191,9 @@ template <int OP> __device__ __forceinline__ bf16 atomic_apply(bf16 *p, bf16 v) 
 }
 
 // ------------------------------------------------------------------ run addressing
-__device__ __forceinline__ int64_t pattern_unit(int64_t base, int64_t sy, int64_t sz, int32_t k, int32_t nx,
-                                                int32_t ny, bool flat) {
-  if (flat) return base + k;
-  const int32_t i = k % nx, jz = k / nx, j = jz % ny, z = jz / ny;
-  return base + i + int64_t(j) * sy + int64_t(z) * sz;
+// floor(n / d) for 0 <= n < 2^31 from d's DivMagic (m, s): one wide multiply and a shift.
+__device__ __forceinline__ int32_t div_by(int32_t n, uint32_t m, int32_t s) {
+  return int32_t((uint64_t(uint32_t(n)) * m) >> s);
 }
 
 struct TsArgs {
@@ -207,6 +205,8 @@ struct TsArgs {
   void *upd;            // FetchAndOp: leafupdate
   int32_t nv;           // vectors per unit
   int32_t phase;        // PH_*
+  uint32_t nv_m;        // DivMagic of nv
+  int32_t nv_s;
 };
 
 // Contiguous tile, copy: n bytes from s to d.  Both are aligned to `gran` bytes; 16-byte
@@ -256,38 +256,40 @@ __device__ __forceinline__ void copy_contiguous(const char *s, char *d, int64_t 
 }
 
 // One CTA per tile of a TS run.  L2R = leaf -> root (Reduce / FetchAndOp), else root -> leaf.
-// Tile-uniform paths: contiguous on both sides (a copy or an element-wise op), contiguous
-// destination with an indexed source (a gather), and the general multi-strided / indexed case.
+// Tile-uniform paths: contiguous on both sides (a copy or an element-wise op), each side
+// contiguous or indexed (gathers and scatters), and the general multi-strided / indexed case.
+// Unit indices, run offsets and strides are below 2^31 (the library's size limit), so they are
+// carried in 32 bits; only unit * nv + v, the vector index, is formed in 64 bits.
 template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
-__device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &r) {
-  const TsTile &t = r;
-  const bool flat = r.nx >= r.n;
+__device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &t) {
+  const bool flat = t.nx >= t.n;
   const int32_t nv = a.nv;
-  const bool ridx = r.flags & RUN_ROOT_IDX, lidx = r.flags & RUN_LEAF_IDX;
+  const bool ridx = t.flags & RUN_ROOT_IDX, lidx = t.flags & RUN_LEAF_IDX;
   // source / destination side descriptions
   bool s_idx = L2R ? lidx : ridx, d_idx = L2R ? ridx : lidx;
   bool s_flat = flat && !s_idx, d_flat = flat && !d_idx;
-  int64_t s0 = L2R ? r.leaf0 : r.root0, d0 = L2R ? r.root0 : r.leaf0;
-  if (a.phase == PH_PACK) { d_flat = true; d_idx = false; d0 = L2R ? r.lbuf0 : r.rbuf0; }
-  if (a.phase == PH_UNPACK) { s_flat = true; s_idx = false; s0 = L2R ? r.rbuf0 : r.lbuf0; }
+  int32_t s0 = L2R ? t.leaf0 : t.root0, d0 = L2R ? t.root0 : t.leaf0;
+  if (a.phase == PH_PACK) { d_flat = true; d_idx = false; d0 = L2R ? t.lbuf0 : t.rbuf0; }
+  if (a.phase == PH_UNPACK) { s_flat = true; s_idx = false; s0 = L2R ? t.rbuf0 : t.lbuf0; }
+  const int32_t work = t.cnt * nv;   // < 2^31: units are at most SF_MAX_UNIT_BYTES
   if constexpr (!ATOMIC) {
     if (s_flat && d_flat) {
+      const int64_t sb = int64_t(s0 + t.k0) * nv, db = int64_t(d0 + t.k0) * nv;
       if constexpr (OP == OP_REPLACE) {
-        copy_contiguous<VB>(static_cast<const char *>(a.src) + (s0 + t.k0) * nv * VB,
-                            static_cast<char *>(a.dst) + (d0 + t.k0) * nv * VB, int64_t(t.cnt) * nv * VB);
+        copy_contiguous<VB>(static_cast<const char *>(a.src) + sb * VB, static_cast<char *>(a.dst) + db * VB,
+                            int64_t(work) * VB);
       } else {
-        const int64_t nvec = int64_t(t.cnt) * nv, sb = (s0 + t.k0) * nv, db = (d0 + t.k0) * nv;
-        for (int64_t base = threadIdx.x; base < nvec; base += int64_t(kThreads) * kUnroll) {
+        for (int32_t base = threadIdx.x; base < work; base += kThreads * kUnroll) {
           Pack<T, VB> x[kUnroll], y[kUnroll];
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u)
-            if (base + u * kThreads < nvec) {
+            if (base + u * kThreads < work) {
               x[u] = ld<T, VB>(a.src, sb + base + u * kThreads);
               y[u] = ld<T, VB>(a.dst, db + base + u * kThreads);
             }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u)
-            if (base + u * kThreads < nvec) st<T, VB>(a.dst, db + base + u * kThreads, combine<OP, T, VB>(y[u], x[u]));
+            if (base + u * kThreads < work) st<T, VB>(a.dst, db + base + u * kThreads, combine<OP, T, VB>(y[u], x[u]));
         }
       }
       return;
@@ -297,95 +299,102 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &r) {
     // each side contiguous or indexed: gathers, scatters, both indexed, atomics
     const int32_t *sidx = (L2R ? a.lidx : a.ridx) + t.idx0 + t.k0;
     const int32_t *didx = (L2R ? a.ridx : a.lidx) + t.idx0 + t.k0;
-    const int64_t sb = s0 + t.k0, db = d0 + t.k0;
-    const int32_t nvec = t.cnt * nv;
+    const int32_t sb = s0 + t.k0, db = d0 + t.k0;
     constexpr int UG = VB >= 16 ? 2 : 4;
-    for (int32_t base = threadIdx.x; base < nvec; base += kThreads * UG) {
-      int64_t si[UG], di[UG];
+    for (int32_t base = threadIdx.x; base < work; base += kThreads * UG) {
+      int32_t su[UG], du[UG], vv[UG];
 #pragma unroll
       for (int u = 0; u < UG; ++u) {
         const int32_t w = base + u * kThreads;
-        const int32_t k = w < nvec ? (nv == 1 ? w : w / nv) : 0;
-        const int32_t v = w < nvec ? w - k * nv : 0;
-        si[u] = (s_idx ? int64_t(__ldg(sidx + k)) : sb + k) * nv + v;
-        di[u] = (d_idx ? int64_t(__ldg(didx + k)) : db + k) * nv + v;
+        const int32_t k = w < work ? (nv == 1 ? w : div_by(w, a.nv_m, a.nv_s)) : 0;
+        vv[u] = w - k * nv;
+        su[u] = s_idx ? __ldg(sidx + k) : sb + k;
+        du[u] = d_idx ? __ldg(didx + k) : db + k;
       }
       Pack<T, VB> x[UG];
 #pragma unroll
       for (int u = 0; u < UG; ++u)
-        if (base + u * kThreads < nvec) x[u] = ld<T, VB>(a.src, si[u]);
+        if (base + u * kThreads < work) x[u] = ld<T, VB>(a.src, int64_t(su[u]) * nv + vv[u]);
       if constexpr (ATOMIC) {
         static_assert(VB == sizeof(T), "atomics are element-wise");
 #pragma unroll
         for (int u = 0; u < UG; ++u)
-          if (base + u * kThreads < nvec) {
-            const T old = atomic_apply<OP>(reinterpret_cast<T *>(a.dst) + di[u], x[u].v[0]);
-            if constexpr (FETCH) reinterpret_cast<T *>(a.upd)[si[u]] = old;   // source side = leaf
+          if (base + u * kThreads < work) {
+            const T old = atomic_apply<OP>(reinterpret_cast<T *>(a.dst) + int64_t(du[u]) * nv + vv[u], x[u].v[0]);
+            if constexpr (FETCH) reinterpret_cast<T *>(a.upd)[int64_t(su[u]) * nv + vv[u]] = old;   // source = leaf
           }
       } else if constexpr (OP == OP_REPLACE) {
 #pragma unroll
         for (int u = 0; u < UG; ++u)
-          if (base + u * kThreads < nvec) st<T, VB>(a.dst, di[u], x[u]);
+          if (base + u * kThreads < work) st<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u], x[u]);
       } else {
         Pack<T, VB> y[UG];
 #pragma unroll
         for (int u = 0; u < UG; ++u)
-          if (base + u * kThreads < nvec) y[u] = ld<T, VB>(a.dst, di[u]);
+          if (base + u * kThreads < work) y[u] = ld<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u]);
 #pragma unroll
         for (int u = 0; u < UG; ++u)
-          if (base + u * kThreads < nvec) st<T, VB>(a.dst, di[u], combine<OP, T, VB>(y[u], x[u]));
+          if (base + u * kThreads < work) st<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u], combine<OP, T, VB>(y[u], x[u]));
       }
     }
     return;
   }
-  // general: pattern or index on either side
-  const int64_t work = int64_t(t.cnt) * nv;
-  for (int64_t base = threadIdx.x; base < work; base += int64_t(kThreads) * kUnroll) {
-    int64_t su[kUnroll], du[kUnroll], lu[kUnroll];
-    int32_t vv[kUnroll];
-    bool ok[kUnroll];
+  // general: pattern or index on either side.  Edge k of the run sits at (i, j, z) of its
+  // nx x ny x nz box, decomposed once for both sides with multiply-shift divisions; a pattern
+  // address is formed modulo 2^32 (exact, since the result is a unit index below 2^31).
+  constexpr int UP = (OP == OP_REPLACE && !ATOMIC && VB < 16) ? 2 : kUnroll;
+  for (int32_t base = threadIdx.x; base < work; base += kThreads * UP) {
+    int32_t su[UP], du[UP], lu[UP], vv[UP];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t w = base + int64_t(u) * kThreads;
-      ok[u] = w < work;
-      const int32_t kl = ok[u] ? int32_t(w / nv) : 0;
-      vv[u] = ok[u] ? int32_t(w - int64_t(kl) * nv) : 0;
+    for (int u = 0; u < UP; ++u) {
+      const int32_t w = base + u * kThreads;
+      const int32_t kl = w >= work ? 0 : nv == 1 ? w : div_by(w, a.nv_m, a.nv_s);
+      vv[u] = w - kl * nv;
       const int32_t k = t.k0 + kl;
-      const int64_t ru = ridx ? int64_t(a.ridx[r.idx0 + k]) : pattern_unit(r.root0, r.rsy, r.rsz, k, r.nx, r.ny, flat);
-      const int64_t leafu = lidx ? int64_t(a.lidx[r.idx0 + k]) : pattern_unit(r.leaf0, r.lsy, r.lsz, k, r.nx, r.ny, flat);
-      int64_t s = L2R ? leafu : ru, d = L2R ? ru : leafu;
-      if (a.phase == PH_PACK) d = (L2R ? r.lbuf0 : r.rbuf0) + k;
-      if (a.phase == PH_UNPACK) s = (L2R ? r.rbuf0 : r.lbuf0) + k;
+      uint32_t i = uint32_t(k), j = 0, z = 0;
+      if (!flat) {
+        const int32_t jz = div_by(k, t.mx, t.sx);
+        i = uint32_t(k - jz * t.nx);
+        z = uint32_t(div_by(jz, t.my, t.sy));
+        j = uint32_t(jz) - z * uint32_t(t.ny);
+      }
+      const int32_t ru = ridx ? __ldg(a.ridx + t.idx0 + k)
+                              : int32_t(uint32_t(t.root0) + i + j * uint32_t(t.rsy) + z * uint32_t(t.rsz));
+      const int32_t leafu = lidx ? __ldg(a.lidx + t.idx0 + k)
+                                 : int32_t(uint32_t(t.leaf0) + i + j * uint32_t(t.lsy) + z * uint32_t(t.lsz));
+      int32_t s = L2R ? leafu : ru, d = L2R ? ru : leafu;
+      if (a.phase == PH_PACK) d = (L2R ? t.lbuf0 : t.rbuf0) + k;
+      if (a.phase == PH_UNPACK) s = (L2R ? t.rbuf0 : t.lbuf0) + k;
       su[u] = s;
       du[u] = d;
       lu[u] = leafu;
     }
-    Pack<T, VB> x[kUnroll];
+    Pack<T, VB> x[UP];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (ok[u]) x[u] = ld<T, VB>(a.src, su[u] * nv + vv[u]);
+    for (int u = 0; u < UP; ++u)
+      if (base + u * kThreads < work) x[u] = ld<T, VB>(a.src, int64_t(su[u]) * nv + vv[u]);
     if constexpr (ATOMIC) {
       static_assert(VB == sizeof(T), "atomics are element-wise");
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
-        if (ok[u]) {
-          T *p = reinterpret_cast<T *>(a.dst) + du[u] * nv + vv[u];
+      for (int u = 0; u < UP; ++u)
+        if (base + u * kThreads < work) {
+          T *p = reinterpret_cast<T *>(a.dst) + int64_t(du[u]) * nv + vv[u];
           const T old = atomic_apply<OP>(p, x[u].v[0]);
-          if constexpr (FETCH) reinterpret_cast<T *>(a.upd)[lu[u] * nv + vv[u]] = old;
+          if constexpr (FETCH) reinterpret_cast<T *>(a.upd)[int64_t(lu[u]) * nv + vv[u]] = old;
         }
     } else {
       if constexpr (OP == OP_REPLACE) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (ok[u]) st<T, VB>(a.dst, du[u] * nv + vv[u], x[u]);
+        for (int u = 0; u < UP; ++u)
+          if (base + u * kThreads < work) st<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u], x[u]);
       } else {
-        Pack<T, VB> y[kUnroll];
+        Pack<T, VB> y[UP];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (ok[u]) y[u] = ld<T, VB>(a.dst, du[u] * nv + vv[u]);
+        for (int u = 0; u < UP; ++u)
+          if (base + u * kThreads < work) y[u] = ld<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u]);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (ok[u]) st<T, VB>(a.dst, du[u] * nv + vv[u], combine<OP, T, VB>(y[u], x[u]));
+        for (int u = 0; u < UP; ++u)
+          if (base + u * kThreads < work) st<T, VB>(a.dst, int64_t(du[u]) * nv + vv[u], combine<OP, T, VB>(y[u], x[u]));
       }
     }
   }
@@ -452,8 +461,64 @@ struct RmArgs {
   void *upd;            // leafupdate (FetchAndOp)
   void *partial;        // scratch: fold partials of multi-block roots
   int32_t *counter;     // scratch: arrivals per (multi-block root, vector); zero between calls
+  int32_t *status;      // device status word of the forest (DEVSTAT_* bits)
   int32_t nv;
+  uint32_t nv_m;        // DivMagic of nv
+  int32_t nv_s;
 };
+
+// ------------------------------------------------------------------ bulk staging into shared memory
+constexpr long long kWaitCycles = 1ll << 31;   // about 1 s at 2 GHz: the bound of every barrier wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Wait until phase `parity` of the mbarrier at shared address `bar` completes, at most `limit`
+// clock cycles; false if it did not.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// Two bulk copies global -> shared (cp.async.bulk: 16-byte aligned addresses, sizes multiples
+// of 16) issued by thread 0, completion counted in bytes on one mbarrier.  Every thread of the
+// CTA calls this and waits; true once the data is in shared memory.  If the wait runs out, the
+// forest's status word gets DEVSTAT_STAGE_TIMEOUT, the copies get one more bounded wait, and
+// the result is false (the caller skips the tile).
+__device__ __forceinline__ bool stage2(void *dst0, const void *src0, uint32_t bytes0, void *dst1, const void *src1,
+                                       uint32_t bytes1, uint64_t *bar, int32_t *status) {
+  const uint32_t b = smem_addr(bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes0 + bytes1) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst0)), "l"(src0), "r"(bytes0), "r"(b) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst1)), "l"(src1), "r"(bytes1), "r"(b) : "memory");
+  }
+  if (mbar_wait(b, 0, kWaitCycles)) return true;
+  if (threadIdx.x == 0 && status) atomicOr(status, DEVSTAT_STAGE_TIMEOUT);
+  mbar_wait(b, 0, kWaitCycles);
+  return false;
+}
+
+// Index load: read-only global path, or a plain load when the indices were staged in shared memory.
+template <bool SM> __device__ __forceinline__ int32_t ld_idx(const int32_t *p) {
+  if constexpr (SM) return *p;
+  else return __ldg(p);
+}
 
 // Expand stored block c (8-byte record plus the next record's first edge) into a Block.
 __device__ __forceinline__ Block load_block(const BlockRec *recs, const Comb *combs, int32_t c) {
@@ -531,20 +596,21 @@ template <int OP, int MODE> struct SingleReads {
 // One fold block of a multi-leaf root, vector v: Bcast writes the root to the block's leaves;
 // Reduce folds the block's leaves in canonical order and either applies the result to the
 // root (single-block root) or leaves a partial whose last arriver folds all partials by D.
-template <typename T, int VB, int OP, int MODE>
-__device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t *m_leaf, const Comb *combs,
-                                           void *partial, int32_t *counter, int32_t nv, const Block b, int32_t v) {
+template <typename T, int VB, int OP, int MODE, bool SM = false>
+__device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t *m_leaf, int32_t lofs,
+                                           const Comb *combs, void *partial, int32_t *counter, int32_t nv,
+                                           const Block b, int32_t v) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
   constexpr int U = VB >= 16 ? 2 : 4;
   const int64_t ri = int64_t(b.root) * nv + v;
-  const int32_t *lidx = m_leaf + b.e0;
+  const int32_t *lidx = m_leaf + (b.e0 - lofs);   // m_leaf holds entries from lofs on
   if constexpr (MODE == RM_BCAST) {
     const Pack<T, VB> x = ld<T, VB>(root, ri);
     for (int32_t e = 0; e < b.n; e += U) {
       int64_t li[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) li[u] = e + u < b.n ? int64_t(__ldg(lidx + e + u)) * nv + v : 0;
+      for (int u = 0; u < U; ++u) li[u] = e + u < b.n ? int64_t(ld_idx<SM>(lidx + e + u)) * nv + v : 0;
       if constexpr (OP == OP_REPLACE) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -569,7 +635,7 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
       Pack<T, VB> y[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (u < b.n) y[u] = ld<T, VB>(leaf, int64_t(__ldg(lidx + u)) * nv + v);
+        if (u < b.n) y[u] = ld<T, VB>(leaf, int64_t(ld_idx<SM>(lidx + u)) * nv + v);
 #pragma unroll
       for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = to_acc<A, T>(y[0].v[l]);
 #pragma unroll
@@ -583,7 +649,7 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
       Pack<T, VB> y[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (e + u < b.n) y[u] = ld<T, VB>(leaf, int64_t(__ldg(lidx + e + u)) * nv + v);
+        if (e + u < b.n) y[u] = ld<T, VB>(leaf, int64_t(ld_idx<SM>(lidx + e + u)) * nv + v);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (e + u < b.n)
@@ -632,8 +698,8 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
 // NB single-block roots folded together (Reduce SUM/MIN/MAX): NB descriptors, then U leaf
 // indices per root, then U leaf values per root are in flight at once, so each thread keeps NB
 // independent load chains going; each root still folds its leaves in canonical order.
-template <typename T, int VB, int OP, int NB>
-__device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t *m_leaf, int32_t nv,
+template <typename T, int VB, int OP, int NB, bool SM = false>
+__device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t *m_leaf, int32_t lofs, int32_t nv,
                                           const Block (&b)[NB], const int32_t (&v)[NB]) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
@@ -651,7 +717,7 @@ __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t 
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int u = 0; u < U; ++u) li[j][u] = e + u < b[j].n ? __ldg(m_leaf + b[j].e0 + e + u) : -1;
+      for (int u = 0; u < U; ++u) li[j][u] = e + u < b[j].n ? ld_idx<SM>(m_leaf + (b[j].e0 - lofs) + e + u) : -1;
     Pack<T, VB> y[NB][U];
 #pragma unroll
     for (int j = 0; j < NB; ++j)
@@ -730,7 +796,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int32_t w = base + u * kThreads;
-        const int32_t kl = nv == 1 ? w : w / nv, v = w - kl * nv;
+        const int32_t kl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - kl * nv;
         on[u] = w < work;
         int64_t ru = 0, lu = 0;
         if (on[u]) {
@@ -761,7 +827,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   } else if (t.kind == T_WINNERS) {
     if constexpr (MODE == RM_REDUCE && OP == OP_REPLACE) {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
-        const int32_t kl = w / nv, v = w - kl * nv, m = t.a + kl;
+        const int32_t kl = div_by(w, a.nv_m, a.nv_s), v = w - kl * nv, m = t.a + kl;
         const int64_t last = a.m_leaf[a.m_ptr[m + 1] - 1];
         st<T, VB>(a.root, int64_t(a.m_root[m]) * nv + v, ld<T, VB>(a.leaf, last * nv + v));
       }
@@ -769,7 +835,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   } else if (t.kind == T_FETCH) {
     if constexpr (MODE == RM_FETCH) {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
-        const int32_t kl = w / nv, v = w - kl * nv, m = t.a + kl;
+        const int32_t kl = div_by(w, a.nv_m, a.nv_s), v = w - kl * nv, m = t.a + kl;
         const int64_t ri = int64_t(a.m_root[m]) * nv + v;
         Pack<T, VB> x = ld<T, VB>(a.root, ri);
         const int32_t e1 = a.m_ptr[m + 1];
@@ -783,35 +849,52 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       }
     }
   } else if (t.kind == T_CHUNKS) {
-    int32_t w = threadIdx.x;
     if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
-      // NB work items per thread (w, w + kThreads, ...), folded together when all are
-      // single-block roots
-      constexpr int NB = VB >= 16 ? 2 : 4;
+      // The tile's block records [a, a + cnt] and leaf entries [k0, e1) are staged in shared
+      // memory by two bulk copies (spans widened to 16-byte boundaries), so each fold issues
+      // only its data loads.  NB work items per thread, folded together when all are
+      // single-block roots.
+      __shared__ alignas(16) BlockRec s_rec[RM_STAGE_RECS];
+      __shared__ alignas(16) int32_t s_leaf[RM_STAGE_LEAVES];
+      __shared__ alignas(8) uint64_t s_bar;
+      const int32_t r0 = t.a & ~1, r1 = (t.a + t.cnt + 2) & ~1;
+      const int32_t l0 = t.k0 & ~3, l1 = int32_t((t.e1 + 3) & ~int64_t(3));
+      if (!stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf, a.m_leaf + l0,
+                  uint32_t(l1 - l0) * 4u, &s_bar, a.status))
+        return;
+      constexpr int NB = 2;
+      int32_t w = threadIdx.x;
       for (; w + (NB - 1) * kThreads < work; w += NB * kThreads) {
         Block b[NB];
         int32_t v[NB];
         bool simple = true;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-          const int32_t wj = w + j * kThreads, cj = nv == 1 ? wj : wj / nv;
+          const int32_t wj = w + j * kThreads, cj = nv == 1 ? wj : div_by(wj, a.nv_m, a.nv_s);
           v[j] = wj - cj * nv;
-          b[j] = load_block(a.blocks, a.combs, t.a + cj);
+          b[j] = load_block(s_rec, a.combs, t.a + cj - r0);
           simple &= b[j].comb < 0;
         }
         if (simple) {
-          fold_many<T, VB, OP, NB>(a.root, a.leaf, a.m_leaf, nv, b, v);
+          fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v);
         } else {
 #pragma unroll
           for (int j = 0; j < NB; ++j)
-            fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv, b[j], v[j]);
+            fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv, b[j],
+                                              v[j]);
         }
       }
-    }
-    for (; w < work; w += kThreads) {
-      const int32_t cl = nv == 1 ? w : w / nv, v = w - cl * nv;
-      fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, a.combs, a.partial, a.counter, nv,
-                                  load_block(a.blocks, a.combs, t.a + cl), v);
+      for (; w < work; w += kThreads) {
+        const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
+        fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
+                                          load_block(s_rec, a.combs, t.a + cl - r0), v);
+      }
+    } else {
+      for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+        const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
+        fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, 0, a.combs, a.partial, a.counter, nv,
+                                    load_block(a.blocks, a.combs, t.a + cl), v);
+      }
     }
   }
 }

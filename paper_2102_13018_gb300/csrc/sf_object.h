@@ -55,6 +55,7 @@ struct sf_s {
   sfgb::DevBuf partial_arg;          // MAX-with-location scratch (leaf units of block maxima)
   sfgb::DevBuf rootbuf, leafbuf;     // three-phase buffers
   sfgb::DevBuf stage_root, stage_leaf;   // memtype staging
+  sfgb::DevBuf status;               // device status word (DEVSTAT_* bits), zero when all is well
   int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
   int32_t tuned_mode = SF_MODE_DETERMINISTIC;   // what AUTO means (sf_autotune may change it)
   int32_t tuned_path = SF_PATH_FUSED;

@@ -15,10 +15,24 @@
 namespace sfgb {
 
 constexpr int FOLD_BLOCK = 64;        // block of the fold D (SF_FOLD_BLOCK)
-constexpr int TS_TILE_EDGES = 4096;   // edges per tile of a TS run
-constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile
+// Tile sizes are powers of two chosen per forest at setup: a launch should have about
+// TILE_TARGET tiles (several waves of 152 SMs x several resident CTAs) so that a small forest
+// still keeps enough loads in flight; large forests use the maxima below, small ones go down to
+// the minima (one unit of work per thread of a 256-thread CTA).
+constexpr int64_t TILE_TARGET = 4096;
+constexpr int TS_TILE_EDGES = 4096;   // edges per tile of a TS run (at most)
+constexpr int TS_TILE_EDGES_MIN = 256;
+constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile (at most)
+constexpr int RM_TILE_EDGES_MIN = 256;
 constexpr int RM_TILE_CHUNKS = 1024;  // fold blocks per chunk tile (at most)
-constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most)
+constexpr int RM_TILE_CHUNKS_MIN = 256;
+constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most), per 1024 blocks
+// A Reduce chunk tile stages its block records [a, a + cnt] and leaf entries [k0, e1) in shared
+// memory with two bulk copies; the spans, widened to 16-byte boundaries, fit these arrays.
+constexpr int RM_STAGE_RECS = RM_TILE_CHUNKS + 4;
+constexpr int RM_STAGE_LEAVES = RM_TILE_CHUNK_EDGES + 8;
+// Device status bits (sf_get_device_status): a bounded wait that ran out.
+constexpr int32_t DEVSTAT_STAGE_TIMEOUT = 1;
 constexpr int RM_TILE_ROOTS = 1024;   // multi roots per winner tile
 constexpr int RM_TILE_FETCH = 128;    // multi roots per fetch tile
 
@@ -57,24 +71,43 @@ enum TileKind : int32_t {
 
 // A slice [k0, k0+cnt) of a TS run with the run's description inlined (one 96-byte load,
 // prefetched by the kernel while it works on the previous tile).
+// A tile of a TS run with the run inline.  Units, strides and edge offsets are below 2^31 (the
+// library's size limit), so the device copy keeps them in 32 bits.
 struct TsTile {
-  int64_t root0, rsy, rsz;
-  int64_t leaf0, lsy, lsz;
-  int64_t idx0, rbuf0, lbuf0;
+  int32_t root0, rsy, rsz;
+  int32_t leaf0, lsy, lsz;
+  int32_t idx0, rbuf0, lbuf0;
   int32_t n, nx, ny, flags;
   int32_t k0, cnt;
+  uint32_t mx, my;   // DivMagic of nx and ny (3-D runs)
+  int32_t sx, sy;
+  int32_t pad;
 };
-static_assert(sizeof(TsTile) == 96, "TsTile is copied in 16-byte pieces");
+static_assert(sizeof(TsTile) == 80, "TsTile is copied in 16-byte pieces");
+
+// Division by a run-time invariant d >= 1 for numerators 0 <= n < 2^31 as one multiply and one
+// shift (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994,
+// Sec. 4): with l = ceil(log2 d) and m = floor(2^(31+l) / d) + 1 (so 2^(31+l) < m d <=
+// 2^(31+l) + 2^l, and m < 2^32), floor(n / d) = floor(n m / 2^(31+l)).
+struct DivMagic {
+  uint32_t m;
+  int32_t s;
+};
+inline DivMagic div_magic(uint32_t d) {
+  int l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  return DivMagic{uint32_t(((uint64_t(1) << (31 + l)) / d) + 1), 31 + l};
+}
 
 // A tile of the root-major plan; masked tiles carry their run inline.
 struct RmTile {
   int32_t kind;              // T_MASKED, T_PAIRS, T_CHUNKS, T_WINNERS, T_FETCH
   int32_t a;                 // first pair / block / multi root
-  int32_t k0;                // masked: first root of the slice inside the run
+  int32_t k0;                // masked: first root of the slice inside the run; chunks: first leaf entry
   int32_t cnt;               // roots / pairs / blocks in the tile
   int64_t root0, leaf0;      // masked run start
   int64_t mask0;             // masked run's first mask bit
-  int64_t pad;
+  int64_t e1;                // chunks: one past the last leaf entry (the span is m_leaf[k0, e1))
 };
 static_assert(sizeof(RmTile) == 48, "RmTile is copied in 16-byte pieces");
 

@@ -213,14 +213,27 @@ struct RunBuilder {
 void push_ts_tiles(std::vector<TsTile> &out, const Run &r, int64_t per) {
   for (int64_t k0 = 0; k0 < r.n; k0 += per) {
     TsTile t{};
-    t.root0 = r.root0; t.rsy = r.rsy; t.rsz = r.rsz;
-    t.leaf0 = r.leaf0; t.lsy = r.lsy; t.lsz = r.lsz;
-    t.idx0 = r.idx0; t.rbuf0 = r.rbuf0; t.lbuf0 = r.lbuf0;
+    // every value below is a unit index, a stride between two units or an edge offset: all
+    // within (-2^31, 2^31) once sizes passed the kMaxUnits checks
+    t.root0 = int32_t(r.root0); t.rsy = int32_t(r.rsy); t.rsz = int32_t(r.rsz);
+    t.leaf0 = int32_t(r.leaf0); t.lsy = int32_t(r.lsy); t.lsz = int32_t(r.lsz);
+    t.idx0 = int32_t(r.idx0); t.rbuf0 = int32_t(r.rbuf0); t.lbuf0 = int32_t(r.lbuf0);
     t.n = r.n; t.nx = r.nx; t.ny = r.ny; t.flags = r.flags;
+    const DivMagic dx = div_magic(uint32_t(std::max(r.nx, 1))), dy = div_magic(uint32_t(std::max(r.ny, 1)));
+    t.mx = dx.m; t.sx = dx.s; t.my = dy.m; t.sy = dy.s;
     t.k0 = int32_t(k0);
     t.cnt = int32_t(std::min<int64_t>(per, r.n - k0));
     out.push_back(t);
   }
+}
+
+// Smallest power of two in [lo, hi] that splits `work` into at most TILE_TARGET tiles (hi if
+// none does).
+int32_t tile_size(int64_t work, int32_t lo, int32_t hi) {
+  const int64_t want = (work + TILE_TARGET - 1) / TILE_TARGET;
+  int64_t s = lo;
+  while (s < want && s < hi) s *= 2;
+  return int32_t(std::min<int64_t>(s, hi));
 }
 
 RmTile rm_tile(int32_t kind, int32_t a, int32_t k0, int32_t cnt) {
@@ -305,10 +318,12 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
         rbuf += t - s;
       }
     }
+    const int32_t ts_per = tile_size(E, TS_TILE_EDGES_MIN, TS_TILE_EDGES);
+    info.ts_tile_edges = ts_per;
     for (size_t r = 0; r < plan.runs.size(); ++r) {
       const Run &run = plan.runs[r];
-      push_ts_tiles(plan.ts_tiles, run, TS_TILE_EDGES);
-      push_ts_tiles((run.flags & RUN_SELF) ? plan.ts_self_tiles : plan.ts_remote_tiles, run, TS_TILE_EDGES);
+      push_ts_tiles(plan.ts_tiles, run, ts_per);
+      push_ts_tiles((run.flags & RUN_SELF) ? plan.ts_self_tiles : plan.ts_remote_tiles, run, ts_per);
       info.runs++;
       const int32_t idx = run.flags & (RUN_ROOT_IDX | RUN_LEAF_IDX);
       if (idx == 0) {
@@ -412,18 +427,25 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
     // tiles, ordered by the first root they touch (heavy multi roots first)
     struct Keyed { int64_t key; RmTile t; };
     std::vector<Keyed> common;
+    int64_t single_work = int64_t(plan.pr_root.size());
+    for (const MaskedRun &mr : plan.mruns) single_work += mr.n;
+    const int32_t rm_per = tile_size(single_work, RM_TILE_EDGES_MIN, RM_TILE_EDGES);   // a multiple of 32
+    const int32_t ch_per = tile_size(int64_t(plan.blocks.size()), RM_TILE_CHUNKS_MIN, RM_TILE_CHUNKS);
+    const int64_t ch_edges = int64_t(RM_TILE_CHUNK_EDGES) * ch_per / RM_TILE_CHUNKS;
+    info.rm_tile_edges = rm_per;
+    info.rm_tile_blocks = ch_per;
     for (size_t i = 0; i < plan.mruns.size(); ++i)
-      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += RM_TILE_EDGES) {
+      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += rm_per) {
         RmTile t = rm_tile(T_MASKED, int32_t(i), int32_t(k0),
-                           int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.mruns[i].n - k0)));
+                           int32_t(std::min<int64_t>(rm_per, plan.mruns[i].n - k0)));
         t.root0 = plan.mruns[i].root0;
         t.leaf0 = plan.mruns[i].leaf0;
         t.mask0 = plan.mruns[i].mask0;
         common.push_back({plan.mruns[i].root0 + k0, t});
       }
-    for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += RM_TILE_EDGES)
+    for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += rm_per)
       common.push_back({plan.pr_root[i], rm_tile(T_PAIRS, int32_t(i), 0,
-                                                 int32_t(std::min<int64_t>(RM_TILE_EDGES, plan.pr_root.size() - i)))});
+                                                 int32_t(std::min<int64_t>(rm_per, plan.pr_root.size() - i)))});
     const int64_t heavy_key = -(int64_t(1) << 40);
     auto finish = [&](std::vector<Keyed> extra, std::vector<RmTile> &out) {
       extra.insert(extra.end(), common.begin(), common.end());
@@ -435,17 +457,20 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       std::vector<Keyed> ch;
       const int64_t nblocks = int64_t(plan.blocks.size());
       int64_t c = 0;
+      // at most ch_per blocks and ch_edges leaf entries per tile (the shared-memory stage)
       while (c < nblocks) {
         const int32_t m = blk_m[c];
         int64_t c1 = c, edges = 0;
         if (heavy[m]) {   // a heavy root's blocks get tiles of their own, scheduled first
-          while (c1 < nblocks && blk_m[c1] == m && c1 - c < RM_TILE_CHUNKS / 4) edges += plan.blocks[c1++].n;
+          while (c1 < nblocks && blk_m[c1] == m && c1 - c < ch_per / 4 && edges + plan.blocks[c1].n <= ch_edges)
+            edges += plan.blocks[c1++].n;
         } else {
-          while (c1 < nblocks && !heavy[blk_m[c1]] && c1 - c < RM_TILE_CHUNKS && edges < RM_TILE_CHUNK_EDGES)
+          while (c1 < nblocks && !heavy[blk_m[c1]] && c1 - c < ch_per && edges + plan.blocks[c1].n <= ch_edges)
             edges += plan.blocks[c1++].n;
         }
-        ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]),
-                      rm_tile(T_CHUNKS, int32_t(c), 0, int32_t(c1 - c))});
+        RmTile t = rm_tile(T_CHUNKS, int32_t(c), plan.blocks[c].e0, int32_t(c1 - c));
+        t.e1 = int64_t(plan.blocks[c].e0) + edges;
+        ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]), t});
         c = c1;
       }
       finish(ch, plan.rm_fold_tiles);

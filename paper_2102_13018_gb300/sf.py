@@ -320,6 +320,12 @@ class StarForest:
         return rootdata
 
 
+    def device_status(self, stream=None) -> int:
+        """Device status bits raised since the previous call (0: none), then cleared; syncs the stream."""
+        st = ctypes.c_int32(0)
+        check(self._lib.sf_get_device_status(self._h, self._stream(stream), ctypes.byref(st)), "sf_get_device_status")
+        return int(st.value)
+
     def reduce_maxloc(self, leafdata, rootdata, argleaf, bs=None, stream=None):
         """rootdata = max over each root's leaves, argleaf = first leaf reaching it (int32)."""
         u = self._unit(rootdata, self.nroots_total, bs)

@@ -137,6 +137,46 @@ def test_spmv_scatter_patterns():
     assert info["rm_masked_runs"] >= P
 
 
+def test_header_constants_match_the_binding():
+    import re
+    from paper_2102_13018_gb300 import _abi
+    text = open(_abi.HEADER).read()
+    for name in ("SF_DEVSTAT_STAGE_TIMEOUT", "SF_MAX_UNIT_BYTES"):
+        m = re.search(r"#define\s+" + name + r"\s+\((\d+) << (\d+)\)|#define\s+" + name + r"\s+(\d+)", text)
+        assert m, name
+        val = int(m.group(1)) << int(m.group(2)) if m.group(1) else int(m.group(3))
+        assert getattr(_abi, name) == val, name
+
+
+def _tile_rule(work, lo, hi, target=4096):
+    """Smallest power of two in [lo, hi] giving at most `target` tiles (hi if none does)."""
+    s = lo
+    while s < hi and -(-work // s) > target:
+        s *= 2
+    return s
+
+
+@pytest.mark.parametrize("n_per_rank", [100, 1 << 16, 300_000, 1 << 22])
+def test_tile_sizes_follow_the_forest_size(n_per_rank):
+    """Tiles shrink with the forest so that a launch has about 4096 of them (powers of two,
+    256..4096 edges; 256..1024 fold blocks), keeping small forests spread over every SM."""
+    f = sfgen.one_to_one(3, 4, n_per_rank)
+    info = StarForest.from_forest(f).analyze().info()
+    E = info["nedges"]
+    assert info["ts_tile_edges"] == _tile_rule(E, 256, 4096)
+    assert info["rm_tile_edges"] == _tile_rule(info["rm_masked_edges"] + info["rm_pairs"], 256, 4096)
+    assert info["rm_tile_blocks"] == _tile_rule(info["rm_chunks"], 256, 1024)
+    if E >= 4096 * 4096:
+        assert info["ts_tile_edges"] == 4096
+
+
+def test_halo_and_spmv_tile_sizes():
+    """The 256^3 halo (1.2M ghost edges) gets 512-edge tiles; the 2^24-root SpMV scatter keeps
+    the 4096-edge maximum."""
+    halo = StarForest.from_forest(sfgen.cfg2_halo()).analyze().info()
+    assert halo["ts_tile_edges"] == 512 and halo["rm_tile_edges"] == 512 and halo["rm_tile_blocks"] == 256
+
+
 def test_operations_before_setup_fail_cleanly():
     lib = _abi.load()
     sf = StarForest.from_forest(sfgen.fig2())

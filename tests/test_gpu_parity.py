@@ -64,6 +64,7 @@ def test_reduce_deterministic_bit_exact(f, op, dtype):
         sf.reduce(l, r, op, bs=bs)
         assert_bits_equal(to_host(r, dtype), want, f"reduce det {f.name} {op} {dtype}x{bs}")
         assert_bits_equal(to_host(l, dtype), leaf, "leafdata must be untouched")
+    assert sf.device_status() == 0
 
 
 @pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
@@ -135,6 +136,7 @@ def test_reduce_heavy_root_recursive_fold():
             r.copy_(to_dev(root, dtype))
             sf.reduce(l, r, "SUM")
             assert_bits_equal(to_host(r, dtype), want, f"heavy star {dtype}")
+    assert sf.device_status() == 0
 
 
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
@@ -196,6 +198,32 @@ def test_misaligned_pointer_rejected():
     u = _abi.sf_unit(_abi.SF_FP64, 1)
     p = ctypes.c_void_p(buf.data_ptr() + 1)
     assert lib.sf_bcast_begin(sf._h, u, p, p, 0, None) == _abi.CODES["SF_ERR_ALIGN"]
+
+
+@pytest.mark.parametrize("dtype,bs", [("fp64", 1 << 16), ("bf16", 1 << 18)])
+def test_largest_unit_matches_oracle(dtype, bs):
+    """Units of exactly 512 KiB (the documented maximum): Bcast REPLACE and deterministic
+    Reduce SUM over every vector of the unit."""
+    f = sfgen.fig2()
+    sf = sf_for(f).set_mode("deterministic")
+    root, leaf = make_data(f, dtype, bs, 810)
+    r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+    sf.bcast(r, l, "REPLACE", bs=bs)
+    assert_bits_equal(to_host(l, dtype), oracle.bcast(f, dtype, bs, root, leaf, "REPLACE"), "bcast max unit")
+    l2 = to_dev(leaf, dtype)
+    sf.reduce(l2, r, "SUM", bs=bs)
+    assert_bits_equal(to_host(r, dtype), oracle.reduce(f, dtype, bs, leaf, root, "SUM"), "reduce max unit")
+
+
+def test_unit_above_the_limit_is_rejected():
+    f = sfgen.fig2()
+    sf = sf_for(f)
+    bs = (1 << 16) + 1                      # fp64: 512 KiB + 8 bytes
+    r = torch.zeros(9 * bs, dtype=torch.float64, device="cuda")
+    l = torch.zeros(11 * bs, dtype=torch.float64, device="cuda")
+    with pytest.raises(SFError) as e:
+        sf.bcast(r, l, "REPLACE", bs=bs)
+    assert e.value.name == "SF_ERR_ARG"
 
 
 def test_launch_counter_advances():
