@@ -401,9 +401,10 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &t) {
 }
 
 // Resident CTAs per SM the register budget must allow: copies are lean, op kernels carry
-// arithmetic and more live state.
+// arithmetic and more live state.  Measured on the 2^24-root Reduce SUM: 4 CTAs of 64
+// registers (a small spill in the rare multi-block combine) beat 3 of 80 (none) and 5 of 48.
 template <int OP, int VB, bool ATOMIC = false> struct MinBlocks {
-  static constexpr int value = ATOMIC ? 4 : OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 3);
+  static constexpr int value = ATOMIC ? 4 : OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 4);
 };
 
 // One CTA per tile (the hardware balances uneven tiles); the tile carries its run inline so a
@@ -752,8 +753,9 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   if (t.kind == T_MASKED && nv == 1) {
     // Scalar units: root, leaf and mask word of an edge are independent loads (every unit in
     // the run's span is valid memory; only the store waits for the mask bit), 8 edges in
-    // flight per thread, 32-bit offsets from the tile's base pointers.
-    constexpr int UM = VB >= 16 ? 4 : 8;
+    // flight per thread for copies, 4 for ops (whose kernels run 4 CTAs per SM), 32-bit
+    // offsets from the tile's base pointers.
+    constexpr int UM = VB >= 16 ? 4 : (OP == OP_REPLACE ? 8 : 4);
     constexpr bool need_root = SingleReads<OP, MODE>::root, need_leaf = SingleReads<OP, MODE>::leaf;
     T *rbase = static_cast<T *>(a.root) + (t.root0 + t.k0) * Pack<T, VB>::L;
     T *lbase = static_cast<T *>(a.leaf) + (t.leaf0 + t.k0) * Pack<T, VB>::L;
