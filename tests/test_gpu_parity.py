@@ -122,6 +122,40 @@ def test_fetch_and_op_atomic_multisf(f, dtype):
         assert np.array_equal(fetched, off[root] + np.arange(deg[root])), root
 
 
+def degree_ladder(nroots=3000, nranks=3, seed=91):
+    """Root r has in-degree (r % 70) + 1: fold blocks of every length 1..64 plus two-block
+    roots, starting at every offset of a 32-leaf warp step; leaves spread over the ranks in
+    random order."""
+    deg = (np.arange(nroots) % 70) + 1
+    owner = np.repeat(np.arange(nroots), deg)
+    perm = np.argsort(sfgen.rng.u64(seed, 1, owner.size), kind="stable")
+    owner = owner[perm]
+    per = -(-nroots // nranks)
+    cuts = np.linspace(0, owner.size, nranks + 1).astype(int)
+    rr = [(owner[cuts[q]:cuts[q + 1]] // per).astype(np.int32) for q in range(nranks)]
+    ri = [(owner[cuts[q]:cuts[q + 1]] % per).astype(np.int64) for q in range(nranks)]
+    roots = np.array([min(per, nroots - p * per) for p in range(nranks)])
+    return sfgen.Forest(nranks, roots, np.diff(cuts), [None] * nranks, rr, ri, name="degree_ladder")
+
+
+LADDER = degree_ladder()
+
+
+@pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
+@pytest.mark.parametrize("dtype", DT)
+def test_reduce_degree_ladder_bit_exact(op, dtype):
+    sf = sf_for(LADDER).set_mode("deterministic")
+    for bs in (1, 2):
+        root, leaf = make_data(LADDER, dtype, bs, 260)
+        r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+        for _ in range(2):          # the second call reuses reset arrival counters
+            r.copy_(to_dev(root, dtype))
+            sf.reduce(l, r, op, bs=bs)
+            assert_bits_equal(to_host(r, dtype), oracle.reduce(LADDER, dtype, bs, leaf, root, op),
+                              f"degree ladder {op} {dtype}x{bs}")
+    assert sf.device_status() == 0
+
+
 def test_reduce_heavy_root_recursive_fold():
     """A star of 300,000 leaves: 4688 blocks -> 74 -> 2 -> 1, three fold levels."""
     n = 300000
