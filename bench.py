@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pingpong", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "halo", "autograd"],
-                    help="run one extra section alone (halo exchange or autograd) and print it")
+    ap.add_argument("--only", default="all", choices=["all", "halo", "autograd", "batched"],
+                    help="run one extra section alone (halo exchange, autograd or the batch) and print it")
     ap.add_argument("--batch-forests", type=int, default=512)
     return ap.parse_args()
 
@@ -471,7 +471,12 @@ def main():
     if args.only != "all":
         # one extra section alone (for profiling it); prints its own JSON object
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        res = run_halo(flush, measured_peak()[0]) if args.only == "halo" else run_autograd(flush)
+        if args.only == "halo":
+            res = run_halo(flush, measured_peak()[0])
+        elif args.only == "batched":
+            res = run_batched(args, torch.cuda.current_stream(), flush)
+        else:
+            res = run_autograd(flush)
         if rank == 0:
             print(json.dumps({"section": args.only, **res}))
         return

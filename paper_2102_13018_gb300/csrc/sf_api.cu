@@ -200,8 +200,7 @@ int bcast_finish(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
 int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s) {
   const int w = elem_size(u.dtype), ub = w * u.bs;
   if (sf->info.nedges == 0) return SF_SUCCESS;
-  const bool atomic = reduce_mode(sf) == SF_MODE_ATOMIC && op != SF_REPLACE && u.dtype != SF_BF16;
-  if (atomic) {
+  if (reduce_atomic(sf, u.dtype, op)) {
     TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
     return launched(launch_ts(u.dtype, op, w, true, true, false, a, sf->dp.n_ts_tiles, s));
   }
@@ -239,6 +238,13 @@ int fetch_launch(sf_t *sf, const sf_unit &u, void *root, const void *leaf, void 
 
 int bcast_path(const sf_t *sf) { return sf->path == SF_PATH_AUTO ? sf->tuned_path : sf->path; }
 int reduce_mode(const sf_t *sf) { return sf->mode == SF_MODE_AUTO ? sf->tuned_mode : sf->mode; }
+
+bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op) {
+  if (op == SF_REPLACE || dtype == SF_BF16) return false;
+  if (reduce_mode(sf) == SF_MODE_ATOMIC) return true;
+  const bool float_sum = op == SF_SUM && (dtype == SF_FP32 || dtype == SF_FP64);
+  return !float_sum && sf->info.max_in_degree <= kOrderFreeMaxDegree;
+}
 
 int ensure_ready(const sf_t *sf) {
   if (!sf) return SF_ERR_NULL;

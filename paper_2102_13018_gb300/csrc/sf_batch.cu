@@ -96,24 +96,23 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
         rm.push_back(rm_args(sf, sf->dp.rm_fold_tiles, sf->dp.n_rm_fold_tiles, const_cast<void *>(root),
                              const_cast<void *>(leaf), nullptr, ub / vbo));
         auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_BCAST, 0, 0}];
-        for (int32_t t = 0; t < sf->dp.n_rm_fold_tiles; ++t) g.push_back(BatchTile{idx, t});
+        for (int32_t t = 0; t < sf->dp.n_rm_fold_tiles; ++t) g.push_back(BatchTile{idx, 0, sf->dp.rm_fold_tiles + t});
       } else {   // fused (the three-phase path is not batched)
         const int idx = int(ts.size());
         ts.push_back(ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, root, const_cast<void *>(leaf), nullptr, ub / vbo,
                              PH_FUSED));
         auto &g = grouped[{stage, 0, o.unit.dtype, o.op, vbo, 0, 0, 0}];
-        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, t});
+        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, 0, sf->dp.ts_tiles + t});
       }
     } else {
       const int mode = reduce_mode(sf);
       modes[i] = mode;
-      const bool atomic = mode == SF_MODE_ATOMIC && o.op != SF_REPLACE && o.unit.dtype != SF_BF16;
-      if (atomic) {
+      if (reduce_atomic(sf, o.unit.dtype, o.op)) {
         const int idx = int(ts.size());
         ts.push_back(ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, const_cast<void *>(root), nullptr, o.unit.bs,
                              PH_FUSED));
         auto &g = grouped[{stage, 0, o.unit.dtype, o.op, w, 0, 1, 1}];
-        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, t});
+        for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, 0, sf->dp.ts_tiles + t});
       } else {
         const int vb = pick_vb(w, ub, true, {root, leaf});
         if (!vb) return SF_ERR_ALIGN;
@@ -132,7 +131,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
         const int idx = int(rm.size());
         rm.push_back(rm_args(sf, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
         auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, 0, 0}];
-        for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, t});
+        for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
       }
     }
   }
@@ -142,8 +141,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
     const sf_batch_op &o = ops[i];
     if (o.kind == SF_OP_BARRIER || o.sf->info.nedges == 0) continue;
     const bool is_rm = (o.kind == SF_OP_BCAST && paths[i] == SF_PATH_ROOT_MAJOR) ||
-                       (o.kind == SF_OP_REDUCE &&
-                        !(modes[i] == SF_MODE_ATOMIC && o.op != SF_REPLACE && o.unit.dtype != SF_BF16));
+                       (o.kind == SF_OP_REDUCE && !reduce_atomic(o.sf, o.unit.dtype, o.op));
     if (is_rm) {
       rm[r].partial = o.sf->partial.p;
       rm[r].counter = static_cast<int32_t *>(o.sf->counter.p);

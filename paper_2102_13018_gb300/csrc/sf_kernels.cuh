@@ -1010,10 +1010,12 @@ __global__ void __launch_bounds__(kThreads) maxloc_scatter_kernel(const int32_t 
 
 // ------------------------------------------------------------------ batched launches
 // Many forests' operations of one kernel variant in one launch: each CTA takes one
-// (operation, tile) pair and runs that forest's tile with that operation's arguments.
+// (operation, tile) pair and runs that forest's tile with that operation's arguments.  The
+// entry points at the tile itself, so the arguments and the tile load side by side.
 struct BatchTile {
-  int32_t op;     // index into the operation table
-  int32_t tile;   // tile of that operation's forest
+  int32_t op;          // index into the operation table
+  int32_t pad;
+  const void *tile;    // TsTile or RmTile of that operation's forest (device address)
 };
 
 template <typename T, int VB, int OP, bool L2R, bool ATOMIC, bool FETCH>
@@ -1021,7 +1023,7 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, ATOMIC>::value))
     ts_batch_kernel(const TsArgs *ops, const BatchTile *tiles) {
   const BatchTile bt = tiles[blockIdx.x];
   const TsArgs a = ops[bt.op];
-  const TsTile t = a.tiles[bt.tile];
+  const TsTile t = *static_cast<const TsTile *>(bt.tile);
   ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
 }
 
@@ -1030,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>
     rm_batch_kernel(const RmArgs *ops, const BatchTile *tiles) {
   const BatchTile bt = tiles[blockIdx.x];
   const RmArgs a = ops[bt.op];
-  const RmTile t = a.tiles[bt.tile];
+  const RmTile t = *static_cast<const RmTile *>(bt.tile);
   rm_tile<T, VB, OP, MODE>(a, t);
 }
 

@@ -77,6 +77,12 @@ TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *
                int phase);
 RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv);
 int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC after resolving AUTO
+// Whether Reduce with `op` on `dtype` runs on the atomic two-sided kernels: in atomic mode
+// (floating SUM rounds in arrival order there), and in deterministic mode for operations whose
+// result does not depend on the order (integer SUM/MIN/MAX, floating MIN/MAX) while no root has
+// more than kOrderFreeMaxDegree leaves (same-address atomics serialise).
+constexpr int64_t kOrderFreeMaxDegree = 1024;
+bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op);
 int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO
 // Enqueue a whole operation (begin and end) on `s`; used by sf_autotune.
 int bcast_all(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s, int path);

@@ -18,12 +18,13 @@ constexpr int FOLD_BLOCK = 64;        // block of the fold D (SF_FOLD_BLOCK)
 // Tile sizes are powers of two chosen per forest at setup: a launch should have about
 // TILE_TARGET tiles (several waves of 152 SMs x several resident CTAs) so that a small forest
 // still keeps enough loads in flight; large forests use the maxima below, small ones go down to
-// the minima (one unit of work per thread of a 256-thread CTA).
+// the minima (two units of work per thread of a 256-thread CTA: 256 was 10% slower on a
+// batch of 512 small forests, 1024 slowed the 1.2M-edge halo).
 constexpr int64_t TILE_TARGET = 4096;
 constexpr int TS_TILE_EDGES = 4096;   // edges per tile of a TS run (at most)
-constexpr int TS_TILE_EDGES_MIN = 256;
+constexpr int TS_TILE_EDGES_MIN = 512;
 constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile (at most)
-constexpr int RM_TILE_EDGES_MIN = 256;
+constexpr int RM_TILE_EDGES_MIN = 512;
 constexpr int RM_TILE_CHUNKS = 1024;  // fold blocks per chunk tile (at most)
 constexpr int RM_TILE_CHUNKS_MIN = 256;
 constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most), per 1024 blocks

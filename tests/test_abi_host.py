@@ -159,12 +159,12 @@ def _tile_rule(work, lo, hi, target=4096):
 @pytest.mark.parametrize("n_per_rank", [100, 1 << 16, 300_000, 1 << 22])
 def test_tile_sizes_follow_the_forest_size(n_per_rank):
     """Tiles shrink with the forest so that a launch has about 4096 of them (powers of two,
-    256..4096 edges; 256..1024 fold blocks), keeping small forests spread over every SM."""
+    512..4096 edges; 256..1024 fold blocks), keeping small forests spread over every SM."""
     f = sfgen.one_to_one(3, 4, n_per_rank)
     info = StarForest.from_forest(f).analyze().info()
     E = info["nedges"]
-    assert info["ts_tile_edges"] == _tile_rule(E, 256, 4096)
-    assert info["rm_tile_edges"] == _tile_rule(info["rm_masked_edges"] + info["rm_pairs"], 256, 4096)
+    assert info["ts_tile_edges"] == _tile_rule(E, 512, 4096)
+    assert info["rm_tile_edges"] == _tile_rule(info["rm_masked_edges"] + info["rm_pairs"], 512, 4096)
     assert info["rm_tile_blocks"] == _tile_rule(info["rm_chunks"], 256, 1024)
     if E >= 4096 * 4096:
         assert info["ts_tile_edges"] == 4096
