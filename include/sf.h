@@ -295,9 +295,11 @@ int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst
 #define SF_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* Deterministic Reduce that allocates nothing.  The paper has no counterpart: this exists for
- * callers that may not allocate device memory at the time of the call -- for example code
- * that runs under a memory budget fixed at start-up, inside a custom allocator's callback, or
- * next to a stream capture that must not see allocations.  sf_reduce_begin/end may grow the
+ * callers that may not allocate device memory at the time of the call -- for example an
+ * application that hands out all device memory from its own pool under a budget fixed at
+ * start-up (a cudaMalloc here would bypass its accounting or fail against its cap), or code
+ * running inside a custom allocator's callback, where a nested cudaMalloc could re-enter that
+ * allocator.  sf_reduce_begin/end may grow the
  * forest's fold scratch with cudaMalloc on the first operation with a wider unit; this call
  * instead keeps the fold partials and arrival counters in one file-scope device array of
  * SF_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until exit.
