@@ -22,7 +22,7 @@ struct Group {
   int stage;
   int family;   // 0 two-sided kernel, 1 root-major kernel
   int dtype, op, vb, mode;
-  bool l2r, atomic;
+  bool l2r, atomic;   // two-sided kernel; for the root-major kernel l2r marks one vector per unit
   size_t tiles_off;   // BatchTile offset in the tile table
   int ntiles;
 };
@@ -130,7 +130,9 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
         const int nt = o.op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
         const int idx = int(rm.size());
         rm.push_back(rm_args(sf, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
-        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, 0, 0}];
+        // one vector per unit: the group runs the Reduce kernel without the multi-vector fold
+        const int nv1 = nv == 1 && o.op != SF_REPLACE && vbo >= 4;
+        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, nv1, 0}];
         for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
       }
     }
@@ -197,7 +199,8 @@ int launch_groups(sf_batch_t *b, cudaStream_t s) {
     if (g.family == 0)
       e = launch_ts(g.dtype, g.op, g.vb, g.l2r, g.atomic, false, TsLaunch{nullptr, b->ts_ops, b->tiles + g.tiles_off, g.ntiles, s});
     else
-      e = launch_rm(g.dtype, g.op, g.vb, g.mode, RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s});
+      e = launch_rm(g.dtype, g.op, g.vb, g.mode,
+                    RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.family == 1 && g.l2r != 0});
     int rc;
     if ((rc = launched(e))) return rc;
   }

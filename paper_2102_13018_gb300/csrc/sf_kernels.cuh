@@ -406,6 +406,10 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &t) {
 template <int OP, int VB, bool ATOMIC = false> struct MinBlocks {
   static constexpr int value = ATOMIC ? 4 : OP == OP_REPLACE ? (VB >= 16 ? 4 : 6) : (VB >= 16 ? 2 : 4);
 };
+// Resident CTAs per SM of the one-vector-unit Reduce kernel (rm_kernel / rm_batch_kernel with
+// NV1): 4 CTAs of 64 registers, no spills; 5 of 48 or 6 of 40 (with smaller gather buffers)
+// measured 16-17% slower on the 2^24-root Reduce SUM.
+constexpr int RM_NV1_BLOCKS = 4;
 
 // One CTA per tile (the hardware balances uneven tiles); the tile carries its run inline so a
 // single descriptor load precedes the data.
@@ -594,6 +598,57 @@ template <int OP, int MODE> struct SingleReads {
   static constexpr bool leaf = !(MODE == RM_BCAST && OP == OP_REPLACE);
 };
 
+// The end of a Reduce fold block whose leaves folded to `acc`: a single-block root gets
+// root op= acc (xr holds the root vector, loaded by the caller); a block of a multi-block root
+// leaves acc as its partial, and the last arriving block of each super-block of FOLD_BLOCK
+// blocks folds that super-block's partials, the last super-block folds those by D and applies
+// the result to the root.
+template <typename T, int VB, int OP>
+__device__ __forceinline__ void fold_finish(void *root, const Comb *combs, void *partial, int32_t *counter,
+                                            int32_t nv, const Block &b, int32_t v,
+                                            Pack<typename Acc<T, OP>::type, int(sizeof(typename Acc<T, OP>::type)) * Pack<T, VB>::L> acc,
+                                            Pack<T, VB> xr) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  const int64_t ri = int64_t(b.root) * nv + v;
+  bool finish = b.comb < 0;
+  if (!finish) {
+    const Comb cb = combs[b.comb];
+    const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;       // block index in the root
+    const int32_t sb = ci / FOLD_BLOCK;                         // super-block
+    const int32_t nsb = (cb.nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
+    const int32_t in_sb = min(FOLD_BLOCK, cb.nch - sb * FOLD_BLOCK);
+    st_cg<A, AVB>(partial, (int64_t(cb.slot) + ci) * nv + v, acc);
+    __threadfence();
+    int32_t *ctr = counter + int64_t(cb.ctr + sb) * nv + v;
+    if (atomicAdd(ctr, 1) == in_sb - 1) {
+      // last block of its super-block: left fold of the super-block's partials
+      __threadfence();
+      acc = fold_range<A, AVB, OP>(partial, int64_t(cb.slot) + sb * FOLD_BLOCK, nv, v, in_sb);
+      *ctr = 0;   // ready for the next operation
+      if (nsb == 1) {
+        finish = true;
+      } else {
+        st_cg<A, AVB>(partial, (int64_t(cb.slot1) + sb) * nv + v, acc);
+        __threadfence();
+        int32_t *rctr = counter + int64_t(cb.ctr + nsb) * nv + v;
+        if (atomicAdd(rctr, 1) == nsb - 1) {
+          __threadfence();
+          acc = fold_partials<A, AVB, OP>(partial, cb.slot1, nv, v, nsb);
+          *rctr = 0;
+          finish = true;
+        }
+      }
+      if (finish) xr = ld<T, VB>(root, ri);
+    }
+  }
+  if (finish) {
+#pragma unroll
+    for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
+    st<T, VB>(root, ri, xr);
+  }
+}
+
 // One fold block of a multi-leaf root, vector v: Bcast writes the root to the block's leaves;
 // Reduce folds the block's leaves in canonical order and either applies the result to the
 // root (single-block root) or leaves a partial whose last arriver folds all partials by D.
@@ -657,41 +712,71 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
 #pragma unroll
           for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
     }
-    bool finish = b.comb < 0;
-    if (!finish) {
-      const Comb cb = combs[b.comb];
-      const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;       // block index in the root
-      const int32_t sb = ci / FOLD_BLOCK;                         // super-block
-      const int32_t nsb = (cb.nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
-      const int32_t in_sb = min(FOLD_BLOCK, cb.nch - sb * FOLD_BLOCK);
-      st_cg<A, AVB>(partial, (int64_t(cb.slot) + ci) * nv + v, acc);
-      __threadfence();
-      int32_t *ctr = counter + int64_t(cb.ctr + sb) * nv + v;
-      if (atomicAdd(ctr, 1) == in_sb - 1) {
-        // last block of its super-block: left fold of the super-block's partials
-        __threadfence();
-        acc = fold_range<A, AVB, OP>(partial, int64_t(cb.slot) + sb * FOLD_BLOCK, nv, v, in_sb);
-        *ctr = 0;   // ready for the next operation
-        if (nsb == 1) {
-          finish = true;
-        } else {
-          st_cg<A, AVB>(partial, (int64_t(cb.slot1) + sb) * nv + v, acc);
-          __threadfence();
-          int32_t *rctr = counter + int64_t(cb.ctr + nsb) * nv + v;
-          if (atomicAdd(rctr, 1) == nsb - 1) {
-            __threadfence();
-            acc = fold_partials<A, AVB, OP>(partial, cb.slot1, nv, v, nsb);
-            *rctr = 0;
-            finish = true;
-          }
-        }
-        if (finish) xr = ld<T, VB>(root, ri);
+    fold_finish<T, VB, OP>(root, combs, partial, counter, nv, b, v, acc, xr);
+  }
+}
+
+// Asynchronous global -> shared copy of one VB-byte vector (cp.async: the data goes to shared
+// memory without passing through registers, so a thread can keep many in flight).  Both
+// addresses are VB-aligned; completion is awaited with cp_async_wait_all.
+template <int VB> __device__ __forceinline__ void cp_async_vec(void *dst_smem, const void *src) {
+  static_assert(VB == 4 || VB == 8 || VB == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(VB)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// A Reduce fold tile of one-vector units (nv == 1), gather-then-fold: with the tile's block
+// records (s_rec, from record r0 on) and leaf entries (s_leaf, from entry l0 on) in shared
+// memory, every thread first issues the root loads of its blocks, then the CTA copies the
+// leaf vectors of the tile's entries into s_val by cp.async -- all of them in flight at once,
+// RM_FLAT_BYTES at a time -- and each thread folds its blocks from shared memory, entry by
+// entry in canonical order (the same left fold as fold_block), carrying the accumulators
+// across rounds.  Every thread of the CTA calls this.
+template <typename T, int VB, int OP>
+__device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t, const BlockRec *s_rec, int32_t r0,
+                                               const int32_t *s_leaf, int32_t l0, Pack<T, VB> *s_val) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  constexpr int R = RM_FLAT_BYTES / VB;                 // leaf vectors per round
+  constexpr int NBT = RM_TILE_CHUNKS / kThreads;        // blocks per thread (a tile has <= RM_TILE_CHUNKS)
+  const int32_t nE = int32_t(t.e1 - t.k0);              // leaf entries of the tile
+  const int32_t *idx = s_leaf + (t.k0 - l0);            // idx[i]: leaf unit of entry k0 + i
+  const BlockRec *rec = s_rec + (t.a - r0);             // rec[w]: block a + w (rec[cnt]: the next one)
+  Pack<T, VB> xr[NBT];
+  Pack<A, AVB> acc[NBT];
+#pragma unroll
+  for (int j = 0; j < NBT; ++j) {
+    const int32_t w = threadIdx.x + j * kThreads;
+    if (w < t.cnt && rec[w].who >= 0) xr[j] = ld<T, VB>(a.root, rec[w].who);   // single-block root
+  }
+  for (int32_t q0 = 0; q0 < nE; q0 += R) {
+    const int32_t nq = min(R, nE - q0);
+    if (q0 > 0) __syncthreads();   // the previous round's vectors are folded
+    for (int32_t k = threadIdx.x; k < nq; k += kThreads)
+      cp_async_vec<VB>(s_val + k, static_cast<const char *>(a.leaf) + int64_t(idx[q0 + k]) * VB);
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NBT; ++j) {
+      const int32_t w = threadIdx.x + j * kThreads;
+      if (w >= t.cnt) continue;
+      const int32_t b0 = rec[w].e0 - t.k0, b1 = rec[w + 1].e0 - t.k0;   // the block's entries
+      const int32_t lo = max(b0, q0), hi = min(b1, q0 + nq);
+      for (int32_t i = lo; i < hi; ++i) {
+        const Pack<T, VB> y = s_val[i - q0];
+#pragma unroll
+        for (int l = 0; l < Pack<T, VB>::L; ++l)
+          acc[j].v[l] = i == b0 ? to_acc<A, T>(y.v[l]) : combine<OP, A>(acc[j].v[l], to_acc<A, T>(y.v[l]));
       }
     }
-    if (finish) {
+  }
 #pragma unroll
-      for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
-      st<T, VB>(root, ri, xr);
+  for (int j = 0; j < NBT; ++j) {
+    const int32_t w = threadIdx.x + j * kThreads;
+    if (w < t.cnt) {
+      const Block b = load_block(rec, a.combs, w);
+      fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, 1, b, 0, acc[j], xr[j]);
     }
   }
 }
@@ -743,12 +828,15 @@ __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t 
   }
 }
 
-template <typename T, int VB, int OP, int MODE>
+// NV1: the launch has one vector per unit (a.nv == 1; Reduce SUM/MIN/MAX with VB >= 4 only),
+// so the multi-vector fold code is left out and the kernel fits a smaller register budget.
+template <typename T, int VB, int OP, int MODE, bool NV1 = false>
 __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
+  static_assert(!NV1 || (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4), "NV1 is a Reduce-op form");
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;   // accumulator pack bytes
   constexpr int U = VB >= 16 ? 2 : 4;
-  const int32_t nv = a.nv;
+  const int32_t nv = NV1 ? 1 : a.nv;
   const int32_t work = t.cnt * nv;
   if (t.kind == T_MASKED && nv == 1) {
     // Scalar units: root, leaf and mask word of an edge are independent loads (every unit in
@@ -858,12 +946,21 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       // single-block roots.
       __shared__ alignas(16) BlockRec s_rec[RM_STAGE_RECS];
       __shared__ alignas(16) int32_t s_leaf[RM_STAGE_LEAVES];
+      __shared__ alignas(16) unsigned char s_val[RM_FLAT_BYTES];
       __shared__ alignas(8) uint64_t s_bar;
       const int32_t r0 = t.a & ~1, r1 = (t.a + t.cnt + 2) & ~1;
       const int32_t l0 = t.k0 & ~3, l1 = int32_t((t.e1 + 3) & ~int64_t(3));
-      if (!stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf, a.m_leaf + l0,
-                  uint32_t(l1 - l0) * 4u, &s_bar, a.status))
-        return;
+      const bool staged = stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf,
+                                 a.m_leaf + l0, uint32_t(l1 - l0) * 4u, &s_bar, a.status);
+      if constexpr (VB >= 4) {
+        if (nv == 1) {   // one vector per unit: gather-then-fold (the CTA agrees on the stage first)
+          if (__syncthreads_and(staged))
+            fold_tile_flat<T, VB, OP>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+          return;
+        }
+      }
+      if constexpr (!NV1) {
+      if (!staged) return;
       constexpr int NB = 2;
       int32_t w = threadIdx.x;
       for (; w + (NB - 1) * kThreads < work; w += NB * kThreads) {
@@ -891,6 +988,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
         fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
                                           load_block(s_rec, a.combs, t.a + cl - r0), v);
       }
+      }   // !NV1
     } else {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
         const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
@@ -901,10 +999,11 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   }
 }
 
-template <typename T, int VB, int OP, int MODE>
-__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>::value)) rm_kernel(RmArgs a) {
+template <typename T, int VB, int OP, int MODE, bool NV1 = false>
+__global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
+    rm_kernel(RmArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
-  rm_tile<T, VB, OP, MODE>(a, t);
+  rm_tile<T, VB, OP, MODE, NV1>(a, t);
 }
 
 // ------------------------------------------------------------------ MAX with location
@@ -1027,13 +1126,13 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, ATOMIC>::value))
   ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
 }
 
-template <typename T, int VB, int OP, int MODE>
-__global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, MODE == RM_FETCH>::value))
+template <typename T, int VB, int OP, int MODE, bool NV1 = false>
+__global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
     rm_batch_kernel(const RmArgs *ops, const BatchTile *tiles) {
   const BatchTile bt = tiles[blockIdx.x];
   const RmArgs a = ops[bt.op];
   const RmTile t = *static_cast<const RmTile *>(bt.tile);
-  rm_tile<T, VB, OP, MODE>(a, t);
+  rm_tile<T, VB, OP, MODE, NV1>(a, t);
 }
 
 }  // namespace sfgb

@@ -23,6 +23,7 @@ struct RmLaunch {
   const BatchTile *tiles;
   int ntiles;
   cudaStream_t s;
+  bool nv1 = false;   // batch: every operation has one vector per unit (Reduce SUM/MIN/MAX, VB >= 4)
 };
 
 // dtype codes are the SF_* codes of sf.h

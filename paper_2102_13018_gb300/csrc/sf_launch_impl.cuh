@@ -15,8 +15,23 @@ cudaError_t go_ts(const TsLaunch &L) {
 template <typename T, int VB, int OP, int MODE>
 cudaError_t go_rm(const RmLaunch &L) {
   if (L.ntiles <= 0) return cudaSuccess;
-  if (L.tiles) rm_batch_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
-  else rm_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+  if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
+    if (L.tiles && L.nv1) {
+      rm_batch_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+      return cudaGetLastError();
+    }
+  }
+  if (L.tiles) {
+    rm_batch_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+    return cudaGetLastError();
+  }
+  if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
+    if (L.single->nv == 1) {
+      rm_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+      return cudaGetLastError();
+    }
+  }
+  rm_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
   return cudaGetLastError();
 }
 

@@ -27,11 +27,15 @@ constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile (at most)
 constexpr int RM_TILE_EDGES_MIN = 512;
 constexpr int RM_TILE_CHUNKS = 1024;  // fold blocks per chunk tile (at most)
 constexpr int RM_TILE_CHUNKS_MIN = 256;
-constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most), per 1024 blocks
+constexpr int RM_TILE_CHUNK_EDGES = 4096;   // leaves per chunk tile (at most), per 1024 blocks
 // A Reduce chunk tile stages its block records [a, a + cnt] and leaf entries [k0, e1) in shared
 // memory with two bulk copies; the spans, widened to 16-byte boundaries, fit these arrays.
 constexpr int RM_STAGE_RECS = RM_TILE_CHUNKS + 4;
 constexpr int RM_STAGE_LEAVES = RM_TILE_CHUNK_EDGES + 8;
+// Leaf vectors a one-vector-unit chunk tile gathers into shared memory per round (bytes): with
+// the two stages above the kernel stays within 48 KB of static shared memory, and four CTAs
+// of the Reduce kernel fit one SM.
+constexpr int RM_FLAT_BYTES = 22 * 1024;
 // Device status bits (sf_get_device_status): a bounded wait that ran out.
 constexpr int32_t DEVSTAT_STAGE_TIMEOUT = 1;
 constexpr int RM_TILE_ROOTS = 1024;   // multi roots per winner tile
@@ -70,8 +74,6 @@ enum TileKind : int32_t {
 };
 
 
-// A slice [k0, k0+cnt) of a TS run with the run's description inlined (one 96-byte load,
-// prefetched by the kernel while it works on the previous tile).
 // A tile of a TS run with the run inline.  Units, strides and edge offsets are below 2^31 (the
 // library's size limit), so the device copy keeps them in 32 bits.
 struct TsTile {
