@@ -323,8 +323,11 @@ int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootda
 int sf_destroy(sf_t *sf);
 
 /* Device status bits of a forest: waits inside the kernels are bounded (about one second);
- * one that runs out sets its bit, skips its tile and lets the kernel finish. */
+ * one that runs out sets its bit, skips its tile and lets the kernel finish.  A kernel also
+ * checks that each tile it stages fits its shared memory, and skips (with a bit) one that does
+ * not -- a plan read by the wrong kernel form, never expected. */
 #define SF_DEVSTAT_STAGE_TIMEOUT 1   /* a bulk copy of plan indices into shared memory did not land */
+#define SF_DEVSTAT_TILE_REFUSED 2    /* a tile larger than the kernel's shared-memory stage was skipped */
 
 /* The forest's device status bits raised since the previous call (0: none), then cleared.
  * Synchronises `stream` (the work the library enqueued on it).  A nonzero status means the

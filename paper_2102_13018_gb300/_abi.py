@@ -18,6 +18,7 @@ SF_OP_BCAST, SF_OP_REDUCE, SF_OP_BARRIER = 0, 1, 2
 SF_FOLD_BLOCK = 64
 SF_NOALLOC_SCRATCH_BYTES = 16 << 20
 SF_DEVSTAT_STAGE_TIMEOUT = 1
+SF_DEVSTAT_TILE_REFUSED = 2
 SF_MAX_UNIT_BYTES = 1 << 19
 
 ERRORS = {0: "SF_SUCCESS", 1: "SF_ERR_ARG", 2: "SF_ERR_NULL", 3: "SF_ERR_RANGE", 4: "SF_ERR_DUP_LEAF",

@@ -214,10 +214,11 @@ int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int3
     const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
     if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
   }
-  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
-  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+  const bool nv1 = reduce_nv1(op, vbo, nv);
+  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
   RmArgs a = rm_args(sf, tiles, nt, root, const_cast<void *>(leaf), nullptr, nv);
-  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, a, nt, s));
+  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
 }
 
 // ---- FetchAndOp ---------------------------------------------------------------------------
@@ -315,7 +316,7 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
                o_segs = b.add(h.segs), o_mv = b.add(sf->h_move_tiles), o_mask = b.add(h.mask),
                o_prr = b.add(h.pr_root), o_prl = b.add(h.pr_leaf), o_mro = b.add(h.m_root), o_mpt = b.add(h.m_ptr),
                o_mle = b.add(h.m_leaf), o_blk = b.add(h.block_recs), o_cmb = b.add(h.combs),
-               o_rf = b.add(h.rm_fold_tiles), o_rw = b.add(h.rm_winner_tiles),
+               o_rf = b.add(h.rm_fold_tiles), o_rf1 = b.add(h.rm_fold_nv1_tiles), o_rw = b.add(h.rm_winner_tiles),
                o_rfe = b.add(h.rm_fetch_tiles);
   const size_t bytes = std::max<size_t>(b.host.size(), 256);
   if (cudaMalloc(&sf->blob.p, bytes) != cudaSuccess) {
@@ -350,9 +351,11 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.blocks = reinterpret_cast<const BlockRec *>(base + o_blk);
   d.combs = reinterpret_cast<const Comb *>(base + o_cmb);
   d.rm_fold_tiles = reinterpret_cast<const RmTile *>(base + o_rf);
+  d.rm_fold_nv1_tiles = reinterpret_cast<const RmTile *>(base + o_rf1);
   d.rm_winner_tiles = reinterpret_cast<const RmTile *>(base + o_rw);
   d.rm_fetch_tiles = reinterpret_cast<const RmTile *>(base + o_rfe);
   d.n_rm_fold_tiles = int32_t(h.rm_fold_tiles.size());
+  d.n_rm_fold_nv1_tiles = int32_t(h.rm_fold_nv1_tiles.size());
   d.n_rm_winner_tiles = int32_t(h.rm_winner_tiles.size());
   d.n_rm_fetch_tiles = int32_t(h.rm_fetch_tiles.size());
   d.n_multi = int32_t(h.m_root.size());
@@ -729,10 +732,11 @@ extern "C" int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(scratch);
   if (cbytes && (rc = cuda_err(cudaMemsetAsync(base + coff, 0, cbytes, s)))) return rc;
-  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
-  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+  const bool nv1 = reduce_nv1(op, vbo, nv);
+  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
   RmArgs a = rm_args(sf, tiles, nt, rootdata, const_cast<void *>(leafdata), nullptr, nv);
   a.partial = base + poff;
   a.counter = reinterpret_cast<int32_t *>(base + coff);
-  return launched(launch_rm(unit.dtype, op, vbo, RM_REDUCE, a, nt, s));
+  return launched(launch_rm(unit.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
 }

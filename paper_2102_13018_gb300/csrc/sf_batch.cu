@@ -126,13 +126,16 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
           const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
           if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
         }
-        const RmTile *rt = o.op == SF_REPLACE ? sf->dp.rm_winner_tiles : sf->dp.rm_fold_tiles;
-        const int nt = o.op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : sf->dp.n_rm_fold_tiles;
+        // one vector per unit: the group runs the Reduce kernel without the multi-vector fold,
+        // on the forest's chunk tiles cut for it
+        const bool nv1 = reduce_nv1(o.op, vbo, nv);
+        const RmTile *rt = o.op == SF_REPLACE ? sf->dp.rm_winner_tiles
+                                              : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
+        const int nt = o.op == SF_REPLACE ? sf->dp.n_rm_winner_tiles
+                                          : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
         const int idx = int(rm.size());
         rm.push_back(rm_args(sf, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
-        // one vector per unit: the group runs the Reduce kernel without the multi-vector fold
-        const int nv1 = nv == 1 && o.op != SF_REPLACE && vbo >= 4;
-        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, nv1, 0}];
+        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, int(nv1), 0}];
         for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
       }
     }

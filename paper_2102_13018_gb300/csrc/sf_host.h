@@ -35,7 +35,7 @@ struct HostPlan {
   std::vector<Block> blocks;         // host view (tiling, statistics)
   std::vector<BlockRec> block_recs;  // device form, one sentinel record at the end
   std::vector<Comb> combs;
-  std::vector<RmTile> rm_fold_tiles, rm_winner_tiles, rm_fetch_tiles;
+  std::vector<RmTile> rm_fold_tiles, rm_fold_nv1_tiles, rm_winner_tiles, rm_fetch_tiles;
   int32_t n_partial_slots = 0, n_counters = 0;
 };
 

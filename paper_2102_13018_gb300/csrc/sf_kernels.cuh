@@ -944,51 +944,54 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       // memory by two bulk copies (spans widened to 16-byte boundaries), so each fold issues
       // only its data loads.  NB work items per thread, folded together when all are
       // single-block roots.
+      constexpr int kStageLeaves = NV1 ? RM_STAGE_LEAVES_NV1 : RM_STAGE_LEAVES;
       __shared__ alignas(16) BlockRec s_rec[RM_STAGE_RECS];
-      __shared__ alignas(16) int32_t s_leaf[RM_STAGE_LEAVES];
-      __shared__ alignas(16) unsigned char s_val[RM_FLAT_BYTES];
+      __shared__ alignas(16) int32_t s_leaf[kStageLeaves];
       __shared__ alignas(8) uint64_t s_bar;
       const int32_t r0 = t.a & ~1, r1 = (t.a + t.cnt + 2) & ~1;
       const int32_t l0 = t.k0 & ~3, l1 = int32_t((t.e1 + 3) & ~int64_t(3));
+      if (t.cnt > RM_TILE_CHUNKS || r1 - r0 > RM_STAGE_RECS || l1 - l0 > kStageLeaves) {
+        // not a tile of this kernel's list (the NV1 form reads rm_fold_nv1_tiles): skip it
+        if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEVSTAT_TILE_REFUSED);
+        return;
+      }
       const bool staged = stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf,
                                  a.m_leaf + l0, uint32_t(l1 - l0) * 4u, &s_bar, a.status);
-      if constexpr (VB >= 4) {
-        if (nv == 1) {   // one vector per unit: gather-then-fold (the CTA agrees on the stage first)
-          if (__syncthreads_and(staged))
-            fold_tile_flat<T, VB, OP>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
-          return;
+      if constexpr (NV1) {   // one vector per unit: gather-then-fold (the CTA agrees on the stage first)
+        __shared__ alignas(16) unsigned char s_val[RM_FLAT_BYTES];
+        if (__syncthreads_and(staged))
+          fold_tile_flat<T, VB, OP>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+        return;
+      } else {
+        if (!staged) return;
+        constexpr int NB = 2;
+        int32_t w = threadIdx.x;
+        for (; w + (NB - 1) * kThreads < work; w += NB * kThreads) {
+          Block b[NB];
+          int32_t v[NB];
+          bool simple = true;
+  #pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            const int32_t wj = w + j * kThreads, cj = nv == 1 ? wj : div_by(wj, a.nv_m, a.nv_s);
+            v[j] = wj - cj * nv;
+            b[j] = load_block(s_rec, a.combs, t.a + cj - r0);
+            simple &= b[j].comb < 0;
+          }
+          if (simple) {
+            fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v);
+          } else {
+  #pragma unroll
+            for (int j = 0; j < NB; ++j)
+              fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv, b[j],
+                                                v[j]);
+          }
+        }
+        for (; w < work; w += kThreads) {
+          const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
+          fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
+                                            load_block(s_rec, a.combs, t.a + cl - r0), v);
         }
       }
-      if constexpr (!NV1) {
-      if (!staged) return;
-      constexpr int NB = 2;
-      int32_t w = threadIdx.x;
-      for (; w + (NB - 1) * kThreads < work; w += NB * kThreads) {
-        Block b[NB];
-        int32_t v[NB];
-        bool simple = true;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          const int32_t wj = w + j * kThreads, cj = nv == 1 ? wj : div_by(wj, a.nv_m, a.nv_s);
-          v[j] = wj - cj * nv;
-          b[j] = load_block(s_rec, a.combs, t.a + cj - r0);
-          simple &= b[j].comb < 0;
-        }
-        if (simple) {
-          fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v);
-        } else {
-#pragma unroll
-          for (int j = 0; j < NB; ++j)
-            fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv, b[j],
-                                              v[j]);
-        }
-      }
-      for (; w < work; w += kThreads) {
-        const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
-        fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
-                                          load_block(s_rec, a.combs, t.a + cl - r0), v);
-      }
-      }   // !NV1
     } else {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
         const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;

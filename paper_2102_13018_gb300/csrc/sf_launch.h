@@ -23,7 +23,7 @@ struct RmLaunch {
   const BatchTile *tiles;
   int ntiles;
   cudaStream_t s;
-  bool nv1 = false;   // batch: every operation has one vector per unit (Reduce SUM/MIN/MAX, VB >= 4)
+  bool nv1 = false;   // the one-vector-unit Reduce kernel (reduce_nv1); its tiles come from rm_fold_nv1_tiles
 };
 
 // dtype codes are the SF_* codes of sf.h

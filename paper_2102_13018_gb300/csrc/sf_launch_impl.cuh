@@ -15,21 +15,22 @@ cudaError_t go_ts(const TsLaunch &L) {
 template <typename T, int VB, int OP, int MODE>
 cudaError_t go_rm(const RmLaunch &L) {
   if (L.ntiles <= 0) return cudaSuccess;
-  if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
-    if (L.tiles && L.nv1) {
-      rm_batch_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+  if (L.nv1) {   // the one-vector-unit kernel; the caller passed tiles of rm_fold_nv1_tiles
+    if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
+      if (L.tiles) {
+        rm_batch_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+      } else {
+        if (L.single->nv != 1) return cudaErrorInvalidValue;
+        rm_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+      }
       return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
     }
   }
   if (L.tiles) {
     rm_batch_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
     return cudaGetLastError();
-  }
-  if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
-    if (L.single->nv == 1) {
-      rm_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
-      return cudaGetLastError();
-    }
   }
   rm_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
   return cudaGetLastError();

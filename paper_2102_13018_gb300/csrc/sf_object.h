@@ -84,6 +84,10 @@ int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC af
 constexpr int64_t kOrderFreeMaxDegree = 1024;
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op);
 int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO
+// Whether a root-major Reduce with `op`, vector width vbo and nv vectors per unit runs the
+// one-vector-unit kernel (NV1), which reads the rm_fold_nv1_tiles list; every caller takes the
+// tile list and the launch flag from this one test.
+inline bool reduce_nv1(int32_t op, int vbo, int nv) { return op != SF_REPLACE && nv == 1 && vbo >= 4; }
 // Enqueue a whole operation (begin and end) on `s`; used by sf_autotune.
 int bcast_all(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s, int path);
 int reduce_all(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int mode);

@@ -27,17 +27,22 @@ constexpr int RM_TILE_EDGES = 4096;   // edges per masked / pairs tile (at most)
 constexpr int RM_TILE_EDGES_MIN = 512;
 constexpr int RM_TILE_CHUNKS = 1024;  // fold blocks per chunk tile (at most)
 constexpr int RM_TILE_CHUNKS_MIN = 256;
-constexpr int RM_TILE_CHUNK_EDGES = 4096;   // leaves per chunk tile (at most), per 1024 blocks
+constexpr int RM_TILE_CHUNK_EDGES = 8192;   // leaves per chunk tile (at most), per 1024 blocks
+// The one-vector-unit Reduce kernel (NV1) reads a second list of chunk tiles, cut at half
+// the leaves, so that its gather buffer fits beside the stages.
+constexpr int RM_TILE_CHUNK_EDGES_NV1 = 4096;
 // A Reduce chunk tile stages its block records [a, a + cnt] and leaf entries [k0, e1) in shared
 // memory with two bulk copies; the spans, widened to 16-byte boundaries, fit these arrays.
 constexpr int RM_STAGE_RECS = RM_TILE_CHUNKS + 4;
 constexpr int RM_STAGE_LEAVES = RM_TILE_CHUNK_EDGES + 8;
-// Leaf vectors a one-vector-unit chunk tile gathers into shared memory per round (bytes): with
-// the two stages above the kernel stays within 48 KB of static shared memory, and four CTAs
-// of the Reduce kernel fit one SM.
+constexpr int RM_STAGE_LEAVES_NV1 = RM_TILE_CHUNK_EDGES_NV1 + 8;
+// Leaf vectors an NV1 chunk tile gathers into shared memory per round (bytes): with its two
+// stages the kernel stays within 48 KB of static shared memory, and four CTAs fit one SM.
 constexpr int RM_FLAT_BYTES = 22 * 1024;
-// Device status bits (sf_get_device_status): a bounded wait that ran out.
+// Device status bits (sf_get_device_status): a bounded wait that ran out; a chunk tile larger
+// than the kernel's stage (a tile list that does not belong to the kernel) that was skipped.
 constexpr int32_t DEVSTAT_STAGE_TIMEOUT = 1;
+constexpr int32_t DEVSTAT_TILE_REFUSED = 2;
 constexpr int RM_TILE_ROOTS = 1024;   // multi roots per winner tile
 constexpr int RM_TILE_FETCH = 128;    // multi roots per fetch tile
 
@@ -169,9 +174,10 @@ struct DevPlan {
   const BlockRec *blocks;                   // fold blocks of multi roots (+ sentinel)
   const Comb *combs;                        // multi roots with several blocks
   const RmTile *rm_fold_tiles;              // masked + pairs + chunks
+  const RmTile *rm_fold_nv1_tiles;          // masked + pairs + chunks of at most RM_TILE_CHUNK_EDGES_NV1
   const RmTile *rm_winner_tiles;            // masked + pairs + winners
   const RmTile *rm_fetch_tiles;             // masked + pairs + fetch
-  int32_t n_rm_fold_tiles, n_rm_winner_tiles, n_rm_fetch_tiles;
+  int32_t n_rm_fold_tiles, n_rm_fold_nv1_tiles, n_rm_winner_tiles, n_rm_fetch_tiles;
   int32_t n_multi, n_partial_slots, n_counters;
 };
 

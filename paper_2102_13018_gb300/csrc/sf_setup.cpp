@@ -431,7 +431,6 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
     for (const MaskedRun &mr : plan.mruns) single_work += mr.n;
     const int32_t rm_per = tile_size(single_work, RM_TILE_EDGES_MIN, RM_TILE_EDGES);   // a multiple of 32
     const int32_t ch_per = tile_size(int64_t(plan.blocks.size()), RM_TILE_CHUNKS_MIN, RM_TILE_CHUNKS);
-    const int64_t ch_edges = int64_t(RM_TILE_CHUNK_EDGES) * ch_per / RM_TILE_CHUNKS;
     info.rm_tile_edges = rm_per;
     info.rm_tile_blocks = ch_per;
     for (size_t i = 0; i < plan.mruns.size(); ++i)
@@ -453,11 +452,14 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       out.clear();
       for (auto &k : extra) out.push_back(k.t);
     };
-    {
+    // chunk tiles: at most ch_per blocks and ch_edges leaf entries per tile (the shared-memory
+    // stage of the kernel that reads them); one list for the general Reduce kernel, one cut at
+    // half the leaves for the one-vector-unit kernel
+    auto chunk_tiles = [&](int64_t max_edges, std::vector<RmTile> &out) {
+      const int64_t ch_edges = max_edges * ch_per / RM_TILE_CHUNKS;
       std::vector<Keyed> ch;
       const int64_t nblocks = int64_t(plan.blocks.size());
       int64_t c = 0;
-      // at most ch_per blocks and ch_edges leaf entries per tile (the shared-memory stage)
       while (c < nblocks) {
         const int32_t m = blk_m[c];
         int64_t c1 = c, edges = 0;
@@ -473,8 +475,10 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
         ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]), t});
         c = c1;
       }
-      finish(ch, plan.rm_fold_tiles);
-    }
+      finish(ch, out);
+    };
+    chunk_tiles(RM_TILE_CHUNK_EDGES, plan.rm_fold_tiles);
+    chunk_tiles(RM_TILE_CHUNK_EDGES_NV1, plan.rm_fold_nv1_tiles);
     {
       std::vector<Keyed> w;
       for (int32_t m = 0; m < M; m += RM_TILE_ROOTS)

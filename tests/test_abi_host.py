@@ -141,7 +141,7 @@ def test_header_constants_match_the_binding():
     import re
     from paper_2102_13018_gb300 import _abi
     text = open(_abi.HEADER).read()
-    for name in ("SF_DEVSTAT_STAGE_TIMEOUT", "SF_MAX_UNIT_BYTES"):
+    for name in ("SF_DEVSTAT_STAGE_TIMEOUT", "SF_DEVSTAT_TILE_REFUSED", "SF_MAX_UNIT_BYTES"):
         m = re.search(r"#define\s+" + name + r"\s+\((\d+) << (\d+)\)|#define\s+" + name + r"\s+(\d+)", text)
         assert m, name
         val = int(m.group(1)) << int(m.group(2)) if m.group(1) else int(m.group(3))
