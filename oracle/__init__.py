@@ -8,7 +8,8 @@ arrays, and follow Sec. III.A-B: Bcast, Reduce and FetchAndOp over edges in cano
 order, with the blocked fold D of block K for floating point Reduce SUM (the paper leaves
 that order open; the reading is stated in sf_oracle.c).
 
-Parity status: every exported function is pinned by tests/test_oracle_pins.py against the
+Parity status: every exported function (Bcast, Reduce, FetchAndOp, Gather, Scatter, the MAX
+with location, the SUM reference) is pinned by tests/test_oracle_pins.py against the
 worked example of Fig. 2, dense incidence-matrix products, library scatter routines,
 closed forms and invariants.
 """
@@ -65,6 +66,8 @@ def _bind(lib):
     lib.oracle_sum_reference.argtypes = [F, i32, i32, vp, vp, vp, vp]
     lib.oracle_reduce_maxloc.argtypes = [F, i32, i32, vp, vp, vp]
     lib.oracle_in_degree.argtypes = [F, vp]
+    lib.oracle_gather.argtypes = [F, i32, i32, vp, vp, vp]
+    lib.oracle_scatter.argtypes = [F, i32, i32, vp, vp]
     lib.oracle_f32_to_bf16.argtypes = [vp, vp, i64]
     lib.oracle_f32_to_bf16.restype = None
     return lib
@@ -206,3 +209,34 @@ def f32_to_bf16(x, lib=None):
     y = np.zeros(x.size, np.uint16)
     lib.oracle_f32_to_bf16(_ptr(x), _ptr(y), x.size)
     return y
+
+
+def gather(forest, dtype: str, bs: int, leafdata, multirootdata, lib=None):
+    """Returns a new multi-root array: multirootdata after Gather (one multi-root per edge;
+    root u's k-th leaf in canonical order lands at (edges into roots below u) + k)."""
+    lib = lib or load()
+    ro, lo = layout(forest, lib)
+    leaf = np.ascontiguousarray(leafdata)
+    multi = np.array(multirootdata, copy=True, order="C")
+    _check(dtype, bs, leaf, lo[-1], "leafdata")
+    _check(dtype, bs, multi, forest.nedges, "multirootdata")
+    m = _Marshalled(forest)
+    n = ctypes.c_int64(-1)
+    rc = lib.oracle_gather(m.ref, DTYPE[dtype], bs, _ptr(leaf), _ptr(multi), ctypes.addressof(n))
+    assert rc == 0 and n.value == forest.nedges
+    return multi
+
+
+def scatter(forest, dtype: str, bs: int, multirootdata, leafdata, lib=None):
+    """Returns a new leaf array: leafdata after Scatter (the reverse of gather; isolated
+    leaves keep their values)."""
+    lib = lib or load()
+    ro, lo = layout(forest, lib)
+    multi = np.ascontiguousarray(multirootdata)
+    leaf = np.array(leafdata, copy=True, order="C")
+    _check(dtype, bs, leaf, lo[-1], "leafdata")
+    _check(dtype, bs, multi, forest.nedges, "multirootdata")
+    m = _Marshalled(forest)
+    rc = lib.oracle_scatter(m.ref, DTYPE[dtype], bs, _ptr(multi), _ptr(leaf))
+    assert rc == 0
+    return leaf

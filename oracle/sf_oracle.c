@@ -408,3 +408,47 @@ int oracle_in_degree(const of_forest *f, int64_t *deg) {
 void oracle_f32_to_bf16(const float *x, uint16_t *y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = f32_to_bf16(x[i]);
 }
+
+/* ---- Gather / Scatter through the multi-forest (Sec. III.B): every root of degree d owns d
+ * consecutive multi-roots, rank-major like the roots (so the multi-root of root unit u is
+ * the number of edges into roots below u, plus k); the k-th leaf of a root in canonical order
+ * goes to its k-th multi-root.  Gather copies leaf units into multirootdata, Scatter copies
+ * them back.  nmulti receives the multi-root count (= edges). ---- */
+static int64_t multi_slots(const of_forest *f, int64_t **slot_out, int64_t **leafu_out) {
+  int64_t *L, *R, NR;
+  int64_t E = edges(f, &L, &R, &NR);
+  int64_t *first = calloc((size_t)NR + 1, sizeof(int64_t)), *slot = malloc(sizeof(int64_t) * (E ? E : 1));
+  for (int64_t e = 0; e < E; ++e) first[R[e] + 1]++;
+  for (int64_t r = 0; r < NR; ++r) first[r + 1] += first[r];     /* edges into roots below r */
+  for (int64_t e = 0; e < E; ++e) slot[e] = first[R[e]]++;       /* canonical order inside a root */
+  free(first);
+  free(R);
+  *slot_out = slot;
+  *leafu_out = L;
+  return E;
+}
+
+int oracle_gather(const of_forest *f, int dtype, int bs, const void *leafdata, void *multirootdata, int64_t *nmulti) {
+  if (!valid(dtype, bs, O_REPLACE)) return 1;
+  int64_t *slot, *L;
+  int64_t E = multi_slots(f, &slot, &L);
+  size_t unit = dsize(dtype) * (size_t)bs;
+  for (int64_t e = 0; e < E; ++e)
+    memcpy((char *)multirootdata + slot[e] * unit, (const char *)leafdata + L[e] * unit, unit);
+  *nmulti = E;
+  free(slot);
+  free(L);
+  return 0;
+}
+
+int oracle_scatter(const of_forest *f, int dtype, int bs, const void *multirootdata, void *leafdata) {
+  if (!valid(dtype, bs, O_REPLACE)) return 1;
+  int64_t *slot, *L;
+  int64_t E = multi_slots(f, &slot, &L);
+  size_t unit = dsize(dtype) * (size_t)bs;
+  for (int64_t e = 0; e < E; ++e)
+    memcpy((char *)leafdata + L[e] * unit, (const char *)multirootdata + slot[e] * unit, unit);
+  free(slot);
+  free(L);
+  return 0;
+}

@@ -30,9 +30,17 @@ MUTANTS = {
     "min_max_swapped": ("else if (op == O_MIN) r = b < a ? b : a;\n      else r = a < b ? b : a;\n      memcpy(dst, &r, 8);\n      break;\n    }\n    case O_BF16",
                         "else if (op == O_MIN) r = a < b ? b : a;\n      else r = b < a ? b : a;\n      memcpy(dst, &r, 8);\n      break;\n    }\n    case O_BF16"),
     "bf16_ties_away": ("(lower == 0x8000u && (upper & 1u))", "(lower == 0x8000u)"),
+    "bf16_min_max_swapped": ("else if (op == O_MIN) hr = b < a ? hb : ha;\n      else hr = a < b ? hb : ha;",
+                             "else if (op == O_MIN) hr = a < b ? hb : ha;\n      else hr = b < a ? hb : ha;"),
+    "bf16_sum_truncated": ("else if (op == O_SUM) hr = f32_to_bf16(a + b);",
+                           "else if (op == O_SUM) { float s = a + b; uint32_t u; memcpy(&u, &s, 4); hr = (uint16_t)(u >> 16); }"),
     "reverse_canonical_order": ("  for (int64_t e = 0; e < E; ++e) perm[fill[R[e]]++] = e;",
                                 "  for (int64_t e = E - 1; e >= 0; --e) perm[fill[R[e]]++] = e;"),
     "edge_root_rank_ignored": ("R[e] = ro[f->rrank[e]] + f->rindex[e];", "R[e] = f->rindex[e];"),
+    "gather_slots_reversed": ("  for (int64_t e = 0; e < E; ++e) slot[e] = first[R[e]]++;",
+                              "  for (int64_t e = E - 1; e >= 0; --e) slot[e] = first[R[e]]++;"),
+    "gather_slot_excludes_own_root": ("for (int64_t r = 0; r < NR; ++r) first[r + 1] += first[r];     /* edges",
+                                      "for (int64_t r = 1; r < NR; ++r) first[r + 1] += first[r - 1];     /* edges"),
 }
 
 
@@ -90,6 +98,27 @@ def battery(lib):
     maxw = np.full(nr, -5.0)
     np.maximum.at(maxw, R, yy[L])
     check("max_scatter", np.array_equal(oracle.reduce(fr, "fp64", 1, yy, np.full(nr, -5.0), "MAX", lib=lib), maxw))
+    # bf16 element op: MAX against numpy on the float32 values, SUM rounded to nearest even
+    yb = (sfgen.data("fp32", nl, 9, 1).view(np.uint32) >> np.uint32(16)).astype(np.uint16)
+    yf = (yb.astype(np.uint32) << np.uint32(16)).view(np.float32)
+    mb = np.full(nr, -5.0, np.float32)
+    np.maximum.at(mb, R, yf[L])
+    got = oracle.reduce(fr, "bf16", 1, yb, np.full(nr, 0xC0A0, np.uint16), "MAX", lib=lib)
+    check("bf16_max_scatter", np.array_equal((got.astype(np.uint32) << np.uint32(16)).view(np.float32), mb))
+    one = sfgen.Forest(1, np.array([1]), np.array([1]), [None], [np.zeros(1, np.int32)], [np.zeros(1, np.int64)])
+    check("bf16_bcast_sum_tie", oracle.bcast(one, "bf16", 1, np.array([0x3B80], np.uint16),
+                                             np.array([0x3F81], np.uint16), "SUM", lib=lib).tolist() == [0x3F82])
+    # Gather / Scatter on Fig. 2 (hand values)
+    try:
+        lo2 = oracle.layout(f, lib)[1]
+        yv2 = np.concatenate([10 * q + np.arange(lo2[q + 1] - lo2[q]) for q in range(3)]).astype(np.int32)
+        mg = oracle.gather(f, "int32", 1, yv2, np.full(f.nedges, -9, np.int32), lib=lib)
+        check("fig2_gather", mg.tolist() == [11, 20, 3, 1, 2, 21, 0, 22, 10, 13])
+        sc = oracle.scatter(f, "int32", 1, 100 + np.arange(f.nedges, dtype=np.int32),
+                            np.full(lo2[-1], -1, np.int32), lib=lib)
+        check("fig2_scatter", sc.tolist() == [106, 103, 104, 102, 108, 100, -1, 109, 101, 105, 107])
+    except Exception:
+        fails.append("gather_crash")
     # bf16 rounding tie
     t = np.array([0x3F808000, 0x3F818000], np.uint32).view(np.float32)
     check("bf16_tie", oracle.f32_to_bf16(t, lib=lib).tolist() == [0x3F80, 0x3F82])

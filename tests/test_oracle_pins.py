@@ -358,3 +358,172 @@ def test_empty_forest_and_isolated():
     assert ro.tolist() == [0, 3, 3] and lo.tolist() == [0, 0, 0]
     r = oracle.reduce(f, "fp64", 1, np.zeros(0), np.array([1.0, 2.0, 3.0]), "SUM")
     assert r.tolist() == [1.0, 2.0, 3.0]
+
+
+# ------------------------------------------------------------------ the bf16 branch of the element op
+def _f32_of_bf16(h):
+    """float32 values of bf16 bit patterns (exact: a bf16 is the top half of a float32)."""
+    return (np.asarray(h, np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def _bf16_full(n, seed, tag, scale=1.0):
+    """n bf16 bit patterns with full 8-bit significands (so sums of two round), made by
+    torch's own float32 -> bfloat16 conversion of uniform float32 values."""
+    torch = pytest.importorskip("torch")
+    x = sfgen.data("fp32", n, seed, tag) * np.float32(scale)
+    return torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+
+
+def _torch_bf16(h):
+    torch = pytest.importorskip("torch")
+    return torch.from_numpy(np.asarray(h, np.uint16).view(np.int16).copy()).view(torch.bfloat16)
+
+
+def _bits(t):
+    return t.view(pytest.importorskip("torch").int16).numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("f", FORESTS + [sfgen.cfg1_plain_tiny()], ids=lambda f: f.name)
+def test_bf16_reduce_min_max_match_numpy_scatter(f):
+    """bf16 Reduce MIN/MAX = numpy minimum.at / maximum.at on the float32 values of the bit
+    patterns (every bf16 is exactly a float32, and the result is one of the inputs)."""
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = _bf16_full(lo[-1] * 2, 23, 1).reshape(-1, 2)
+    r0 = _bf16_full(ro[-1] * 2, 23, 2).reshape(-1, 2)
+    for op, ufunc in (("MIN", np.minimum), ("MAX", np.maximum)):
+        want = _f32_of_bf16(r0).copy()
+        ufunc.at(want, R, _f32_of_bf16(y)[L])
+        got = oracle.reduce(f, "bf16", 2, y.ravel(), r0.ravel(), op).reshape(-1, 2)
+        assert np.array_equal(_f32_of_bf16(got), want), op
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
+def test_bf16_bcast_ops_match_torch(f, op):
+    """bf16 Bcast with an op: each leaf takes one root, combined and rounded by torch's own
+    CPU bfloat16 arithmetic (SUM rounds the float32 sum to nearest even)."""
+    torch = pytest.importorskip("torch")
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    x = _bf16_full(ro[-1] * 3, 24, 1, 4.0).reshape(-1, 3)
+    leaf0 = _bf16_full(lo[-1] * 3, 24, 2, 4.0).reshape(-1, 3)
+    lt, xt = _torch_bf16(leaf0), _torch_bf16(x)
+    fn = {"SUM": torch.add, "MIN": torch.minimum, "MAX": torch.maximum}[op]
+    want = lt.clone()
+    idx_l, idx_r = torch.from_numpy(L), torch.from_numpy(R)
+    want[idx_l] = fn(lt[idx_l], xt[idx_r])
+    got = oracle.bcast(f, "bf16", 3, x.ravel(), leaf0.ravel(), op).reshape(-1, 3)
+    assert np.array_equal(got, _bits(want))
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_bf16_fetch_and_op_sum_rounds_every_op(f):
+    """bf16 FetchAndOp SUM is a chain of bf16 additions, each rounded: replayed edge by edge
+    in canonical order with torch CPU bfloat16 scalars."""
+    torch = pytest.importorskip("torch")
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = _bf16_full(lo[-1], 25, 1)
+    r0 = _bf16_full(ro[-1], 25, 2, 8.0)
+    r = _torch_bf16(r0).clone()
+    yt = _torch_bf16(y)
+    upd = torch.zeros(lo[-1], dtype=torch.bfloat16)
+    for e in range(len(L)):
+        upd[L[e]] = r[R[e]]
+        r[R[e]] = r[R[e]] + yt[L[e]]
+    got_r, got_u = oracle.fetch_and_op(f, "bf16", 1, r0, y, np.zeros(lo[-1], np.uint16), "SUM")
+    connected = np.zeros(lo[-1], bool)
+    connected[L] = True
+    assert np.array_equal(got_r, _bits(r))
+    assert np.array_equal(got_u[connected], _bits(upd)[connected])
+
+
+def test_bf16_rounding_per_op_differs_from_rounding_once():
+    """Hand values.  bf16 has 8 significand bits, so 256 + 1 = 257 is a tie between 256 and
+    258 and rounds to the even 256.  FetchAndOp SUM of leaves (1, 1) into root 256 rounds after
+    each op: 256 -> 256 -> 256, fetching (256, 256).  Reduce SUM folds the leaves in float32
+    first and rounds once: 256 + 2 = 258.  Bcast SUM of root 1 into leaf 256 gives 256, and
+    1.0078125 + 2^-8 (a tie between 1.0078125 and 1.015625) gives the even 1.015625."""
+    f = star(2)
+    b256, b1, b258 = 0x4380, 0x3F80, 0x4381
+    root, upd = oracle.fetch_and_op(f, "bf16", 1, np.array([b256], np.uint16), np.array([b1, b1], np.uint16),
+                                    np.zeros(2, np.uint16), "SUM")
+    assert root.tolist() == [b256] and upd.tolist() == [b256, b256]
+    red = oracle.reduce(f, "bf16", 1, np.array([b1, b1], np.uint16), np.array([b256], np.uint16), "SUM")
+    assert red.tolist() == [b258]
+    one = sfgen.Forest(1, np.array([1]), np.array([1]), [None], [np.zeros(1, np.int32)], [np.zeros(1, np.int64)])
+    assert oracle.bcast(one, "bf16", 1, np.array([b1], np.uint16), np.array([b256], np.uint16),
+                        "SUM").tolist() == [b256]
+    assert oracle.bcast(one, "bf16", 1, np.array([0x3B80], np.uint16), np.array([0x3F81], np.uint16),
+                        "SUM").tolist() == [0x3F82]
+
+
+def test_max_ties_keep_the_first_value_in_canonical_order():
+    """MAX(a, b) = (a < b ? b : a) keeps the current value on a tie, so +0 and -0 (equal)
+    resolve by order: the root keeps its own zero when a leaf brings the other one, and a root
+    below zero takes the first zero in canonical order."""
+    f = star(3)
+    pz, nz = 0.0, -0.0
+    got = oracle.reduce(f, "fp64", 1, np.array([nz, pz, nz]), np.array([-1.0]), "MAX")
+    assert np.signbit(got[0])
+    got = oracle.reduce(f, "fp64", 1, np.array([pz, nz, nz]), np.array([-1.0]), "MAX")
+    assert got[0] == 0.0 and not np.signbit(got[0])
+    got = oracle.reduce(f, "fp64", 1, np.array([pz, pz, pz]), np.array([nz]), "MAX")
+    assert np.signbit(got[0])
+    got = oracle.reduce(f, "fp32", 1, np.array([nz, pz, nz], np.float32), np.array([1.0], np.float32), "MIN")
+    assert np.signbit(got[0])
+
+
+def test_nan_leaf_never_wins_min_max():
+    """The element op compares with < only, so a NaN leaf loses every MIN/MAX against a
+    non-NaN root (NaN < x and x < NaN are both false).  NaN input is outside the library's
+    contract for MIN/MAX; this pins what the oracle computes."""
+    f = star(3)
+    got = oracle.reduce(f, "fp64", 1, np.array([np.nan, 2.0, np.nan]), np.array([1.0]), "MAX")
+    assert got[0] == 2.0
+    got = oracle.reduce(f, "fp64", 1, np.array([np.nan, 0.5, np.nan]), np.array([1.0]), "MIN")
+    assert got[0] == 0.5
+
+
+# ------------------------------------------------------------------ Gather / Scatter (multi-forest)
+def test_fig2_gather_and_scatter():
+    f = sfgen.fig2()
+    ro, lo = oracle.layout(f)
+    g = GOLD["gather"]
+    y = _fig2_leafvals(lo).astype(np.int32)
+    multi = oracle.gather(f, "int32", 1, y, np.full(f.nedges, -9, np.int32))
+    assert split(multi, g["multirootoff"]) == g["multiroots"]
+    back = oracle.scatter(f, "int32", 1, 100 + np.arange(f.nedges, dtype=np.int32), np.full(lo[-1], -1, np.int32))
+    assert split(back, lo) == GOLD["scatter"]["leaves"]
+
+
+@pytest.mark.parametrize("f", FORESTS + [sfgen.cfg1_plain_tiny()], ids=lambda f: f.name)
+def test_gather_is_a_stable_sort_by_root_and_scatter_inverts_it(f):
+    """Gather lists the leaf units grouped by root, canonical order inside a root (a stable
+    argsort of the root units); Scatter puts them back (isolated leaves untouched)."""
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = sfgen.data("fp64", lo[-1] * 2, 26, 1).reshape(-1, 2)
+    order = np.argsort(R, kind="stable")
+    multi = oracle.gather(f, "fp64", 2, y.ravel(), np.zeros(len(L) * 2)).reshape(-1, 2)
+    assert np.array_equal(multi, y[L[order]])
+    leaf0 = sfgen.data("fp64", lo[-1] * 2, 26, 2).reshape(-1, 2)
+    back = oracle.scatter(f, "fp64", 2, multi.ravel(), leaf0.ravel()).reshape(-1, 2)
+    want = leaf0.copy()
+    want[L] = y[L]
+    assert np.array_equal(back, want)
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+def test_gather_slots_are_the_fetch_and_op_multisf_offsets(f):
+    """The paper's recipe (Sec. III.B): FetchAndOp SUM with roots at degree-prefix offsets and
+    leaves of 1 fetches, for every leaf, its multi-root; Gather must put the leaf there."""
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    deg = np.bincount(R, minlength=ro[-1])
+    off = np.concatenate([[0], np.cumsum(deg)[:-1]]).astype(np.int64)
+    _, slot = oracle.fetch_and_op(f, "int64", 1, off, np.ones(lo[-1], np.int64), np.full(lo[-1], -1, np.int64), "SUM")
+    y = sfgen.data("int64", lo[-1], 27, 1, "wide")
+    multi = oracle.gather(f, "int64", 1, y, np.zeros(len(L), np.int64))
+    assert np.array_equal(multi[slot[L]], y[L])
