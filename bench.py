@@ -79,6 +79,57 @@ def algorithmic_bytes(info, unit_bytes=8):
     return bcast, reduce
 
 
+def op_bytes(info, kind, op, unit_bytes):
+    """Algorithmic bytes of one operation: Bcast reads each connected root once and writes every
+    leaf (and reads it for an op other than REPLACE); Reduce reads every leaf and reads and
+    writes each connected root; FetchAndOp adds the leafupdate writes; plus the index words."""
+    idx = 4 * (info["edges_one_indexed"] + 2 * info["edges_two_indexed"])
+    U, E, C = unit_bytes, info["nedges"], info["connected_roots"]
+    if kind == "bcast":
+        return U * C + U * E * (1 if op == "REPLACE" else 2) + idx
+    if kind == "reduce":
+        return U * E + 2 * U * C + idx
+    return U * E + 2 * U * C + U * E + idx
+
+
+def time_op(fn, stream, flush=None, reps=30, warm=3):
+    """Median CUDA-event time (ms) of fn() on `stream`, each call alone (after an L2 flush if
+    a flush buffer is given)."""
+    import torch
+    ts = []
+    for i in range(reps + warm):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warm:
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip().lower(), v.strip())
+        return fields.get("model name") or f"implementer {fields.get('cpu implementer')} part {fields.get('cpu part')}"
+    except OSError:
+        return "unknown"
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -274,6 +325,64 @@ def run_batched(args, stream, flush):
             "graph_gbs": nbytes / (t_graph * 1e-3) / 1e9, "speedup_graph_vs_per_forest": t_per / t_graph}
 
 
+def run_tiny(stream):
+    """The plain tiny forest (4 ranks x 4096 roots, 16384 uniform leaves): every operation of
+    the workload in int32 and fp64, bs = 1, each call timed alone.  Its 0.3 MB sit in L2, so
+    these are launch- and L2-bound times (us) and L2-resident GB/s, not HBM figures."""
+    import torch
+    import sfgen
+    from paper_2102_13018_gb300 import StarForest
+    f = sfgen.cfg1_plain_tiny()
+    sf = StarForest.from_forest(f).setup().set_mode("deterministic")
+    info = sf.info()
+    out = {"workload": "plain_tiny: 4 ranks x 4096 roots, 16384 leaves uniform over all roots, bs=1",
+           "l2": "resident (no flush)"}
+    for dt, tdt, w in (("int32", torch.int32, 4), ("fp64", torch.float64, 8)):
+        x = (torch.rand(sf.nroots_total, device="cuda") * 1000).to(tdt)
+        lv = (torch.rand(sf.leaf_extent, device="cuda") * 1000).to(tdt)
+        upd = torch.zeros_like(lv)
+        cases = [("bcast_replace", "bcast", "REPLACE", lambda: sf.bcast(x, lv, "REPLACE", stream=stream)),
+                 ("bcast_sum", "bcast", "SUM", lambda: sf.bcast(x, lv, "SUM", stream=stream)),
+                 ("reduce_sum", "reduce", "SUM", lambda: sf.reduce(lv, x, "SUM", stream=stream)),
+                 ("reduce_max", "reduce", "MAX", lambda: sf.reduce(lv, x, "MAX", stream=stream)),
+                 ("fetch_and_op_sum", "fetch", "SUM", lambda: sf.fetch_and_op(x, lv, upd, "SUM", stream=stream))]
+        for label, kind, op, fn in cases:
+            ms = time_op(fn, stream, None, reps=200, warm=10)
+            nb = op_bytes(info, kind, op, w)
+            out[f"{label}_{dt}"] = {"us": ms * 1e3, "bytes": nb, "l2_gbs": nb / (ms * 1e-3) / 1e9}
+    return out
+
+
+def abi_call_cost(sf, x, lv, n=20000):
+    """Host time per Begin+End pair of the 1 KB ping-pong Bcast: straight through ctypes with the
+    arguments built once (the C ABI's own cost plus the kernel launch it enqueues), and through
+    the Python StarForest wrapper (argument marshalling added).  The kernel is a ~2 us copy, so
+    the loop is bound by the host."""
+    import ctypes
+    import torch
+    lib = sf._lib
+    args = (sf._h, sf._unit(x, sf.nroots_total, None), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(lv.data_ptr()),
+            0, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    begin, end = lib.sf_bcast_begin, lib.sf_bcast_end
+    for _ in range(1000):
+        begin(*args)
+        end(*args)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        begin(*args)
+        end(*args)
+    t_abi = (time.perf_counter() - t0) / n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        sf.bcast(x, lv, "REPLACE")
+    t_py = (time.perf_counter() - t0) / n
+    torch.cuda.synchronize()
+    return {"ctypes_prebuilt_us": t_abi * 1e6, "python_wrapper_us": t_py * 1e6,
+            "what": "host time per Bcast Begin+End (one kernel launch), 1 KB forest"}
+
+
 def run_pingpong(stream):
     """Sec. VI.A ping-pong on one GPU: n fp64 roots on rank 0 connected consecutively to n leaves
     on rank 1; one round trip is Bcast REPLACE then Reduce REPLACE (the roots come back
@@ -324,17 +433,23 @@ def run_pingpong(stream):
         torch.cuda.synchronize()
         graph_us = e0.elapsed_time(e1) * 1e3 / reps
         out[f"{nbytes // 1024}K"] = {"plain_us": plain_us, "graph_us": graph_us}
+        if nbytes == 1 << 10:
+            out["abi_call_cost_1K"] = abi_call_cost(sf, x, lv)
     return {"what": "round trip Bcast REPLACE + Reduce REPLACE, contiguous 2-rank forest, fp64, one GPU",
             "paper_table1_sf_dd_us": {"1K": 22.8, "4K": 23.0, "16K": 22.9, "64K": 23.5, "256K": 27.7,
                                       "1024K": 46.3, "4096K": 111.8},
             "sizes": out}
 
 
-def run_autograd(flush):
-    """Differentiable message passing on the power-law graph (2^20 roots, 2^23 leaves, bs = 64):
-    forward Bcast then backward (Reduce SUM of the leaf gradient) through the library's
-    autograd functions, against the same computation written with plain PyTorch ops
-    (index_select forward, index_add_ backward -- atomic, not reproducible)."""
+def run_autograd(flush, peak):
+    """Differentiable message passing on the power-law graph (2^20 roots, 2^23 leaves, bs = 64),
+    through the library's autograd functions, fp32 and bf16: Bcast, Reduce SUM and Reduce MAX,
+    each forward + backward, against the same computation in plain PyTorch (index_select /
+    index_add_ / scatter_reduce: atomic, not reproducible).  Algorithmic bytes (U = 64 x element
+    size, E leaves, C connected roots, NR roots, 4 bytes per index):
+      Bcast fwd U(C + E) + 4E, bwd (Reduce SUM from zero) U(E + NR) + 4E;
+      Reduce SUM fwd U(E + NR) + 4E, bwd (Bcast) U(C + E) + 4E;
+      Reduce MAX fwd U(E + NR) + 4E + 256 NR (argmax), bwd U(NR + E) + 256 NR."""
     import numpy as np
     import torch
     import sfgen
@@ -346,41 +461,44 @@ def run_autograd(flush):
     idx = torch.from_numpy(np.concatenate([f.iremote_rank[q].astype(np.int64) * per + f.iremote_index[q]
                                            for q in range(f.nranks)])).cuda()
     info = sf.info()
+    E, C, NR, bs = info["nedges"], info["connected_roots"], sf.nroots_total, 64
     out = {}
     for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
-        x = torch.rand(sf.nroots_total, 64, device="cuda").to(dt).requires_grad_(True)
-        g = torch.rand(sf.leaf_extent, 64, device="cuda").to(dt)
-        ub = 64 * x.element_size()
-        fwd_bytes = ub * info["connected_roots"] + ub * info["nedges"] + 4 * info["nedges"]
-        bwd_bytes = ub * info["nedges"] + 2 * ub * info["connected_roots"] + 4 * info["nedges"]
+        U = bs * torch.tensor([], dtype=dt).element_size()
+        x = torch.rand(NR, bs, device="cuda").to(dt).requires_grad_(True)
+        y = torch.rand(sf.leaf_extent, bs, device="cuda").to(dt).requires_grad_(True)
+        gl = torch.rand(sf.leaf_extent, bs, device="cuda").to(dt)
+        gr = torch.rand(NR, bs, device="cuda").to(dt)
+        bytes_ = {"bcast": U * (C + E) + 4 * E + U * (E + NR) + 4 * E,
+                  "reduce_sum": U * (E + NR) + 4 * E + U * (C + E) + 4 * E,
+                  "reduce_max": U * (E + NR) + 4 * E + 4 * bs * NR + U * (NR + E) + 4 * bs * NR}
 
-        def ours():
-            x.grad = None
-            sfa.bcast(sf, x).backward(g)
+        def run(fn, t):
+            t.grad = None
+            fn()
 
-        def plain():
-            x.grad = None
-            torch.index_select(x, 0, idx).backward(g)
-
+        cases = {
+            "bcast": (lambda: run(lambda: sfa.bcast(sf, x).backward(gl), x),
+                      lambda: run(lambda: torch.index_select(x, 0, idx).backward(gl), x)),
+            "reduce_sum": (lambda: run(lambda: sfa.reduce(sf, y, "SUM").backward(gr), y),
+                           lambda: run(lambda: torch.zeros(NR, bs, device="cuda", dtype=dt)
+                                       .index_add(0, idx, y).backward(gr), y)),
+            "reduce_max": (lambda: run(lambda: sfa.reduce(sf, y, "MAX").backward(gr), y),
+                           lambda: run(lambda: torch.zeros(NR, bs, device="cuda", dtype=dt).scatter_reduce(
+                               0, idx[:, None].expand(-1, bs), y, "amax", include_self=False).backward(gr), y)),
+        }
         res = {}
-        for label, fn in (("sf_autograd", ours), ("torch_index_select_add", plain)):
-            for _ in range(3):
-                fn()
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(10):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn()
-                e1.record()
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            ms = statistics.median(ts)
-            res[label] = {"ms": ms, "gbs": (fwd_bytes + bwd_bytes) / (ms * 1e-3) / 1e9}
+        for label, (ours, plain) in cases.items():
+            r = {}
+            for who, fn in (("sf_autograd", ours), ("torch", plain)):
+                ms = time_op(fn, torch.cuda.current_stream(), flush, reps=10, warm=3)
+                gbs = bytes_[label] / (ms * 1e-3) / 1e9
+                r[who] = {"ms": ms, "gbs": gbs, "frac": gbs / peak}
+            r["bytes"] = bytes_[label]
+            res[label] = r
         out[name] = res
     return {"workload": "power-law message passing: 2^20 roots, 2^23 leaves (Chung-Lu, exponent 2.2), "
-                        "bs=64; forward Bcast + backward Reduce SUM", **out}
+                        "bs=64; forward + backward of Bcast, Reduce SUM and Reduce MAX", **out}
 
 
 def run_halo(flush, peak):
@@ -424,6 +542,90 @@ def run_halo(flush, peak):
             gbs = nbytes / (us * 1e-6) / 1e9
             out[f"{label}_bs{bs}"] = {"us": us, "gbs": gbs, "frac": gbs / peak}
     return out
+
+
+def run_fp32_step(sf, info, x, y, stream, flush, peak, steps):
+    """The benchmark step in fp32 on the same forest (bs = 1, 4-byte units): Bcast REPLACE then
+    the deterministic Reduce SUM, each op timed with CUDA events, L2 flushed between steps."""
+    import torch
+    x32, y32 = x.float(), y.float()
+    l32 = torch.zeros(sf.leaf_extent, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        flush.zero_()
+        sf.bcast(x32, l32, "REPLACE", stream=stream)
+        sf.reduce(l32, y32, "SUM", stream=stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        sf.bcast(x32, l32, "REPLACE", stream=stream)
+        ev[i][1].record(stream)
+        sf.reduce(l32, y32, "SUM", stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    b = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    r = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    bb, rb = algorithmic_bytes(info, 4)
+    return {"dtype": "f32", "steps": steps, "ms_per_step": b + r, "gbs": (bb + rb) / ((b + r) * 1e-3) / 1e9,
+            "frac": (bb + rb) / ((b + r) * 1e-3) / 1e9 / peak, "bcast_ms": b, "reduce_ms": r,
+            "bcast_frac": bb / (b * 1e-3) / 1e9 / peak, "reduce_frac": rb / (r * 1e-3) / 1e9 / peak}
+
+
+def cpu_parallel_baseline(forest, x_h, y_h, step_bytes):
+    """The step on all host cores (OpenMP, oracle/sf_cpu_parallel.c): a baseline, not a path of
+    the library."""
+    import numpy as np
+    import oracle
+    try:
+        cp = oracle.CpuParallel(forest)
+    except RuntimeError as e:
+        return {"kind": "openmp", "unavailable": str(e)}
+    lv = np.zeros(int(oracle.layout(forest)[1][-1]))
+    y = y_h.copy()
+    cp.bcast_replace(x_h, lv)
+    cp.reduce_sum(lv, y)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 10.0 and reps < 50:
+        cp.bcast_replace(x_h, lv)
+        cp.reduce_sum(lv, y)
+        reps += 1
+    secs = (time.perf_counter() - t0) / reps
+    return {"value": step_bytes / secs / 1e9, "unit": "GB/s", "cores": cp.threads, "kind": "openmp",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "ms_per_step": secs * 1e3,
+            "sample": f"the full workload, {reps} steps of one Bcast REPLACE + one deterministic Reduce SUM"}
+
+
+def sum_error_statement(sf, forest, stream):
+    """Reduce SUM on the full workload against the oracle's fp64 reference (Neumaier-compensated
+    r0 + sum of the leaves): the largest absolute and relative (to |r0| + sum |y|) error, and the
+    largest error over the bound tol x in-degree x (|r0| + sum |y|), atomic and deterministic."""
+    import numpy as np
+    import torch
+    import oracle
+    import sfgen
+    tol = {"fp32": 1e-6, "fp64": 1e-13}
+    deg = np.maximum(oracle.in_degree(forest), 1).astype(np.float64)
+    ro, lo = oracle.layout(forest)
+    out = {}
+    for dt in ("fp64", "fp32"):
+        leaf = sfgen.data(dt, int(lo[-1]), 5, 1)
+        root = sfgen.data(dt, int(ro[-1]), 5, 2)
+        ref, absum = oracle.sum_reference(forest, dt, 1, leaf, root)
+        lt = torch.from_numpy(leaf).cuda()
+        for mode in ("atomic", "deterministic"):
+            sf.set_mode(mode)
+            r = torch.from_numpy(root).cuda()
+            sf.reduce(lt, r, "SUM", stream=stream)
+            err = np.abs(r.cpu().numpy().astype(np.float64) - ref)
+            out[f"{dt}_{mode}"] = {"max_abs": float(err.max()),
+                                   "max_rel": float((err / np.maximum(absum, 1e-300)).max()),
+                                   "max_over_bound": float((err / (tol[dt] * deg * np.maximum(absum, 1e-300))).max()),
+                                   "tol": tol[dt]}
+    sf.set_mode("deterministic")
+    return {"what": "Reduce SUM of uniform [-1,1) data, full workload, vs the oracle's fp64 compensated sum; "
+                    "bound = tol x in-degree x (|r0| + sum |y|)", **out}
 
 
 def max_over_ranks(local_ms: float, world: int, device: str = "cpu") -> float:
@@ -476,7 +678,7 @@ def main():
         elif args.only == "batched":
             res = run_batched(args, torch.cuda.current_stream(), flush)
         else:
-            res = run_autograd(flush)
+            res = run_autograd(flush, measured_peak()[0])
         if rank == 0:
             print(json.dumps({"section": args.only, **res}))
         return
@@ -539,9 +741,12 @@ def main():
     value = job_value(bb + rb, K, max_ms, world)
     peak, peak_src = measured_peak()
     b_avg, r_avg = statistics.mean(bcast_ms), statistics.mean(reduce_ms)
-    dom = ("rm_kernel", rb, r_avg) if r_avg >= b_avg else ("ts_kernel", bb, b_avg)
+    # the deterministic Reduce is one launch: the diagonal-chunk kernel when the plan covers
+    # every connected root, else the root-major kernel
+    rk = "dg_kernel" if info["dg_chunks"] > 0 and info["dg_rest_roots"] == 0 else "rm_kernel"
+    dom = (rk, rb, r_avg) if r_avg >= b_avg else ("ts_kernel", bb, b_avg)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom[0] + (" (Reduce SUM, deterministic)" if dom[0] == "rm_kernel"
+    roofline = {"bound": "hbm", "kernel": dom[0] + (" (Reduce SUM, deterministic)" if dom[0] != "ts_kernel"
                                                     else " (Bcast REPLACE, fused)"),
                 "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": committed_traffic(dom[0]),
@@ -554,73 +759,72 @@ def main():
     # the other data paths on the same forest, timed the same way (not part of the step)
     variants = {}
     if not args.no_variants:
-        def time_op(fn, reps=30):
-            ts = []
-            for i in range(reps + 3):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if i >= 3:
-                    ts.append(e0.elapsed_time(e1))
-            return statistics.median(ts)
         for path in ("fused", "three_phase", "root_major"):
             sf.set_path(path)
-            ms = time_op(lambda: sf.bcast(x, lvec, "REPLACE", stream=stream))
+            ms = time_op(lambda: sf.bcast(x, lvec, "REPLACE", stream=stream), stream, flush)
             variants[f"bcast_{path}"] = {"ms": ms, "gbs": bb / (ms * 1e-3) / 1e9}
         sf.set_path("fused")
         for mode in ("deterministic", "atomic"):
             sf.set_mode(mode)
-            ms = time_op(lambda: sf.reduce(lvec, y, "SUM", stream=stream))
+            ms = time_op(lambda: sf.reduce(lvec, y, "SUM", stream=stream), stream, flush)
             variants[f"reduce_sum_{mode}"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
         sf.set_mode("deterministic")
         ms = time_op(lambda: sf._lib.sf_reduce_noalloc(sf._h, sf._unit(y, sf.nroots_total, None),
-                                                      sf._ptr(lvec), sf._ptr(y), 1, sf._stream(stream)))
+                                                      sf._ptr(lvec), sf._ptr(y), 1, sf._stream(stream)), stream, flush)
         variants["reduce_sum_noalloc"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
+        # FetchAndOp SUM on the same forest: each root's leaves fetch its running sum
+        fb = op_bytes(info, "fetch", "SUM", 8)
+        upd = torch.zeros(nl, dtype=torch.float64, device="cuda")
+        for mode in ("deterministic", "atomic"):
+            sf.set_mode(mode)
+            ms = time_op(lambda: sf.fetch_and_op(y, lvec, upd, "SUM", stream=stream), stream, flush)
+            variants[f"fetch_and_op_sum_{mode}"] = {"ms": ms, "bytes": fb, "gbs": fb / (ms * 1e-3) / 1e9}
+        sf.set_mode("deterministic")
+        variants["fp32"] = run_fp32_step(sf, info, x, y, stream, flush, peak, max(3, min(K, 50)))
 
-    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    # end to end through the public API, as an SpMV caller runs the step: x and y in pinned host
+    # memory, the work vector lvec on the device (copies inside the timed region, the host
+    # waiting for y every step)
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(x_h).pin_memory()
         yh = torch.from_numpy(y_h).pin_memory()
-        lh = torch.zeros(nl, dtype=torch.float64).pin_memory()
         for _ in range(2):
-            sf.bcast_memtype(xh, lh, "REPLACE", stream=stream)
-            sf.reduce_memtype(lh, yh, "SUM", stream=stream)
+            sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
+            sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
         torch.cuda.synchronize()
         Ke = max(3, min(K, 50))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(Ke):
-            sf.bcast_memtype(xh, lh, "REPLACE", stream=stream)
-            sf.reduce_memtype(lh, yh, "SUM", stream=stream)
+            sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
+            sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
             stream.synchronize()
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1) / Ke
-        # Bcast: x in (leaves are all written by REPLACE, so not copied in), lvec out;
-        # Reduce: lvec in, y in, y out
-        h2d = 8 * nr + 8 * nl + 8 * nr
-        d2h = 8 * nl + 8 * nr
+        # Bcast: x in; Reduce: y in, y out
+        h2d = 8 * nr + 8 * nr
+        d2h = 8 * nr
         e2e = {"value": world * (bb + rb) / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke,
+               "what": "x, y pinned host (sf_*_with_memtype), lvec on the device, host waits for y every step"}
 
     pingpong = None
     if not args.no_pingpong:
         pingpong = run_pingpong(stream)
 
-    autograd = halo = None
+    autograd = halo = tiny = None
     if not args.no_extras:
-        autograd = run_autograd(flush)
+        autograd = run_autograd(flush, peak)
         halo = run_halo(flush, peak)
+        tiny = run_tiny(stream)
 
     batched = None
     if not args.no_batched:
         batched = run_batched(args, stream, flush)
 
-    cpu = None
+    cpu = cpu_all = sum_error = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         lv0 = np.zeros(nl)
@@ -628,18 +832,24 @@ def main():
         reps = max(1, min(10, int(20.0 / max(secs, 1e-3))))
         secs = oracle_step_time(forest, x_h, lv0, y_h, reps=reps) if reps > 1 else secs
         cpu = {"value": (bb + rb) / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                "sample": f"the full workload, {reps} step(s) of one Bcast REPLACE + one Reduce SUM"}
+        cpu_all = cpu_parallel_baseline(forest, x_h, y_h, bb + rb)
+        sum_error = sum_error_statement(sf, forest, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, forest),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+                "sum_error_vs_fp64_reference": sum_error, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "ops": ops, "variants": variants, "batched": batched,
-                "pingpong": pingpong, "autograd": autograd, "halo": halo,
+                "pingpong": pingpong, "autograd": autograd, "halo": halo, "plain_tiny": tiny,
                 "plan": {k: info[k] for k in ("nedges", "connected_roots", "multi_roots", "multi_edges",
                                               "edges_both_pattern", "edges_one_indexed", "edges_two_indexed",
-                                              "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes")}}
+                                              "rm_masked_edges", "rm_pairs", "rm_chunks", "dg_chunks", "dg_roots",
+                                              "dg_extra_leaves", "dg_list_roots", "dg_rest_roots",
+                                              "device_plan_bytes")}}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

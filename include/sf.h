@@ -54,7 +54,12 @@ typedef struct {
   int32_t bs;
 } sf_unit;
 
-/* Reduction operators of Sec. III.B (MPI_REPLACE, MPI_SUM, MPI_MIN, MPI_MAX). */
+/* Reduction operators of Sec. III.B (MPI_REPLACE, MPI_SUM, MPI_MIN, MPI_MAX).
+ * op(a, b) with a the current value and b the incoming one: REPLACE b, SUM a + b (integers
+ * wrap around), MIN (b < a ? b : a), MAX (a < b ? b : a).  On a tie MIN/MAX keep the current
+ * value, so equal floating values with different bits (+0 and -0) resolve by the order the
+ * operation applies them (canonical edge order in SF_MODE_DETERMINISTIC).  Floating MIN/MAX of
+ * NaN input is undefined: the deterministic fold may let a NaN leaf hide the leaves after it. */
 enum { SF_REPLACE = 0, SF_SUM = 1, SF_MIN = 2, SF_MAX = 3 };
 
 /* How Reduce combines several leaves of one root (Sec. V.C uses atomics on duplicates).
@@ -129,6 +134,11 @@ typedef struct {
   int64_t ts_tile_edges;       /* edges per tile of a two-sided run (smaller forests: smaller tiles) */
   int64_t rm_tile_edges;       /* edges per masked / single-leaf tile of the root-major plan */
   int64_t rm_tile_blocks;      /* fold blocks per chunk tile of the root-major plan (at most) */
+  int64_t dg_chunks;           /* diagonal-chunk plan of the deterministic Reduce: 32-root chunks (0: none) */
+  int64_t dg_roots;            /* roots it covers (each with its leaf at root + a per-chunk offset) */
+  int64_t dg_extra_leaves;     /* their other leaves */
+  int64_t dg_list_roots;       /* of those roots, with more than one other leaf */
+  int64_t dg_rest_roots;       /* connected roots it leaves to the root-major plan */
 } sf_info;
 
 /* Create a star forest (PetscSFCreate + PetscSFSetGraph, Sec. III.A).
@@ -174,6 +184,21 @@ int sf_reduce_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata
                     sf_stream_t stream);
 int sf_reduce_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
                   sf_stream_t stream);
+
+/* Reduce into roots that start at zero: the result is what sf_reduce_begin/end compute after
+ * rootdata was set to zero (with the forest's mode; roots without leaves end at 0), but the old
+ * rootdata is never read, and only the roots without leaves are written twice -- cheaper than a
+ * memset of the whole root buffer followed by a Reduce.  The functional form the adjoint of
+ * Bcast needs (Sec. IV.A: y = P^T lvec).  Same begin/end rules as sf_reduce_begin/end. */
+int sf_reduce_from_zero_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                              sf_stream_t stream);
+int sf_reduce_from_zero_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                            sf_stream_t stream);
+
+/* Set every root without leaves to 0 (all bs elements), and, when argleaf is not NULL, its bs
+ * entries of argleaf (int32[nroots_total * bs]) to -1; other roots are not touched.  Together
+ * with sf_reduce_maxloc this gives the functional MAX with location over every root. */
+int sf_zero_leafless_roots(sf_t *sf, sf_unit unit, void *rootdata, int32_t *argleaf, sf_stream_t stream);
 
 /* FetchAndOp (Sec. III.B): for each root, its leaves are applied one at a time; before leaf
  * e is applied, the root's current value is stored into leafupdate[leaf e]:

@@ -39,13 +39,69 @@ FOLD_BLOCK = 64
 GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 
+_PAR_SRC = os.path.join(_HERE, "sf_cpu_parallel.c")
+_PAR_LIB = os.path.join(_HERE, "_build", "libsf_cpu_parallel.so")
+
+
 def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
+    if src == _SRC:
+        build_parallel(force)
     return out
+
+
+def build_parallel(force: bool = False):
+    """The multi-core CPU baseline of the benchmark (sf_cpu_parallel.c, OpenMP).  Returns its
+    path, or None when the compiler has no OpenMP (the baseline is then reported missing)."""
+    if not force and os.path.exists(_PAR_LIB) and os.path.getmtime(_PAR_LIB) >= os.path.getmtime(_PAR_SRC):
+        return _PAR_LIB
+    tmp = _PAR_LIB + f".{os.getpid()}.tmp"
+    r = subprocess.run(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                        "-fno-fast-math", "-o", tmp, _PAR_SRC], capture_output=True)
+    if r.returncode != 0:
+        return None
+    os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+class CpuParallel:
+    """The benchmark step on all host cores (bench.py's multi-core CPU baseline; fp64, bs = 1):
+    bcast_replace(root, leaf) and reduce_sum(leaf, root), in place.  Not the oracle."""
+
+    def __init__(self, forest):
+        path = build_parallel()
+        if path is None:
+            raise RuntimeError("no OpenMP compiler for the multi-core CPU baseline")
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        lib.cp_plan_create.argtypes = [ctypes.POINTER(_Forest)]
+        lib.cp_plan_create.restype = vp
+        lib.cp_plan_destroy.argtypes = [vp]
+        lib.cp_bcast_replace_f64.argtypes = [vp, vp, vp]
+        lib.cp_reduce_sum_f64.argtypes = [vp, vp, vp]
+        lib.cp_threads.restype = ctypes.c_int
+        self._lib = lib
+        m = _Marshalled(forest)
+        self._plan = lib.cp_plan_create(m.ref)
+        self.threads = int(lib.cp_threads())
+
+    def bcast_replace(self, root, leaf):
+        assert root.dtype == np.float64 and leaf.dtype == np.float64 and leaf.flags.c_contiguous
+        self._lib.cp_bcast_replace_f64(self._plan, _ptr(np.ascontiguousarray(root)), _ptr(leaf))
+
+    def reduce_sum(self, leaf, root):
+        assert root.dtype == np.float64 and leaf.dtype == np.float64 and root.flags.c_contiguous
+        self._lib.cp_reduce_sum_f64(self._plan, _ptr(np.ascontiguousarray(leaf)), _ptr(root))
+
+    def __del__(self):
+        try:
+            self._lib.cp_plan_destroy(self._plan)
+        except Exception:
+            pass
 
 
 class _Forest(ctypes.Structure):

@@ -55,7 +55,8 @@ class sf_info(ctypes.Structure):
                    "multi_roots", "multi_edges", "segments", "self_edges", "runs", "runs_pattern", "runs_3d",
                    "edges_both_pattern", "edges_one_indexed", "edges_two_indexed", "rm_masked_runs",
                    "rm_masked_edges", "rm_pairs", "rm_chunks", "device_plan_bytes", "ts_tile_edges",
-                   "rm_tile_edges", "rm_tile_blocks")]
+                   "rm_tile_edges", "rm_tile_blocks", "dg_chunks", "dg_roots", "dg_extra_leaves", "dg_list_roots",
+                   "dg_rest_roots")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -90,7 +91,9 @@ def load():
     lib.sf_get_info.argtypes = [vp, P(sf_info)]
     lib.sf_set_mode.argtypes = [vp, i32]
     lib.sf_set_path.argtypes = [vp, i32]
-    for name in ("sf_bcast_begin", "sf_bcast_end", "sf_reduce_begin", "sf_reduce_end"):
+    lib.sf_zero_leafless_roots.argtypes = [vp, sf_unit, vp, vp, vp]
+    for name in ("sf_bcast_begin", "sf_bcast_end", "sf_reduce_begin", "sf_reduce_end", "sf_reduce_from_zero_begin",
+                 "sf_reduce_from_zero_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, vp, vp, i32, vp]
     for name in ("sf_fetch_and_op_begin", "sf_fetch_and_op_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, vp, vp, vp, i32, vp]

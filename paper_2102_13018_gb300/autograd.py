@@ -5,6 +5,10 @@ lvec = P x), so its adjoint is Reduce with SUM (y = P^T lvec), and vice versa.  
 each root's gradient to the first leaf, in canonical order, that reached the maximum.  Units
 are rows of bs elements; fp32 and bf16 storage both accumulate in fp32 (bf16 Reduce SUM rounds
 once per result).  Roots without leaves get 0 in the functional forms and no gradient.
+
+Outputs are allocated uninitialised and written whole by the library: the Reduce runs from
+zero (roots never read, roots without leaves zeroed by the library), and a Bcast output is
+zero-filled only when some leaf of the layout has no root.
 """
 from __future__ import annotations
 
@@ -19,12 +23,19 @@ def _units(t: torch.Tensor, n: int):
     return t.numel() // max(n, 1)
 
 
+def _leaf_out(sf: StarForest, bs: int, like: torch.Tensor) -> torch.Tensor:
+    """The output of a Bcast REPLACE: uninitialised when every leaf has a root (all are written),
+    else zeros (leaves without a root keep 0)."""
+    make = torch.empty if sf.all_leaves_connected() else torch.zeros
+    return make(sf.leaf_extent, bs, dtype=like.dtype, device=like.device)
+
+
 class _Bcast(torch.autograd.Function):
     @staticmethod
     def forward(ctx, root, sf: StarForest):
         bs = _units(root, sf.nroots_total)
         root = root.contiguous()
-        leaf = torch.zeros(sf.leaf_extent, bs, dtype=root.dtype, device=root.device)
+        leaf = _leaf_out(sf, bs, root)
         sf.bcast(root, leaf, "REPLACE", bs=bs)
         ctx.sf, ctx.bs = sf, bs
         return leaf
@@ -32,8 +43,8 @@ class _Bcast(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         sf, bs = ctx.sf, ctx.bs
-        groot = torch.zeros(sf.nroots_total, bs, dtype=g.dtype, device=g.device)
-        sf.reduce(g.contiguous(), groot, "SUM", bs=bs)
+        groot = torch.empty(sf.nroots_total, bs, dtype=g.dtype, device=g.device)
+        sf.reduce_from_zero(g.contiguous(), groot, "SUM", bs=bs)
         return groot, None
 
 
@@ -42,15 +53,15 @@ class _ReduceSum(torch.autograd.Function):
     def forward(ctx, leaf, sf: StarForest):
         bs = _units(leaf, sf.leaf_extent)
         leaf = leaf.contiguous()
-        root = torch.zeros(sf.nroots_total, bs, dtype=leaf.dtype, device=leaf.device)
-        sf.reduce(leaf, root, "SUM", bs=bs)
+        root = torch.empty(sf.nroots_total, bs, dtype=leaf.dtype, device=leaf.device)
+        sf.reduce_from_zero(leaf, root, "SUM", bs=bs)
         ctx.sf, ctx.bs = sf, bs
         return root
 
     @staticmethod
     def backward(ctx, g):
         sf, bs = ctx.sf, ctx.bs
-        gleaf = torch.zeros(sf.leaf_extent, bs, dtype=g.dtype, device=g.device)
+        gleaf = _leaf_out(sf, bs, g)
         sf.bcast(g.contiguous(), gleaf, "REPLACE", bs=bs)
         return gleaf, None
 
@@ -60,8 +71,9 @@ class _ReduceMax(torch.autograd.Function):
     def forward(ctx, leaf, sf: StarForest):
         bs = _units(leaf, sf.leaf_extent)
         leaf = leaf.contiguous()
-        root = torch.zeros(sf.nroots_total, bs, dtype=leaf.dtype, device=leaf.device)
-        arg = torch.full((sf.nroots_total, bs), -1, dtype=torch.int32, device=leaf.device)
+        root = torch.empty(sf.nroots_total, bs, dtype=leaf.dtype, device=leaf.device)
+        arg = torch.empty((sf.nroots_total, bs), dtype=torch.int32, device=leaf.device)
+        sf.zero_leafless_roots(root, arg, bs=bs)
         sf.reduce_maxloc(leaf, root, arg, bs=bs)
         ctx.sf, ctx.bs = sf, bs
         ctx.save_for_backward(arg)

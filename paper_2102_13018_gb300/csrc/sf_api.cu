@@ -121,15 +121,20 @@ TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *
 }
 
 RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv) {
+  return rm_args_plan(sf, sf->dp, tiles, ntiles, root, leaf, upd, nv);
+}
+
+RmArgs rm_args_plan(sf_t *sf, const DevPlan &d, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd,
+                    int nv) {
   RmArgs a{};
-  a.mask = sf->dp.mask;
-  a.pr_root = sf->dp.pr_root;
-  a.pr_leaf = sf->dp.pr_leaf;
-  a.m_root = sf->dp.m_root;
-  a.m_ptr = sf->dp.m_ptr;
-  a.m_leaf = sf->dp.m_leaf;
-  a.blocks = sf->dp.blocks;
-  a.combs = sf->dp.combs;
+  a.mask = d.mask;
+  a.pr_root = d.pr_root;
+  a.pr_leaf = d.pr_leaf;
+  a.m_root = d.m_root;
+  a.m_ptr = d.m_ptr;
+  a.m_leaf = d.m_leaf;
+  a.blocks = d.blocks;
+  a.combs = d.combs;
   a.tiles = tiles;
   a.ntiles = ntiles;
   a.root = root;
@@ -197,28 +202,87 @@ int bcast_finish(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
 }
 
 // ---- Reduce -------------------------------------------------------------------------------
-int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s) {
+DgArgs dg_args(const sf_t *sf, const void *leaf, void *root) {
+  DgArgs g{};
+  g.chunks = sf->dp.dg_chunks;
+  g.x = sf->dp.dg_x;
+  g.lists = sf->dp.dg_lists;
+  g.c0 = sf->dp.dg_c0;
+  g.nchunks = sf->dp.dg_nchunks;
+  g.nroots = int32_t(sf->info.nroots_total);
+  g.ntiles = (sf->dp.dg_nchunks + DG_TILE_CHUNKS - 1) / DG_TILE_CHUNKS;
+  g.root = root;
+  g.leaf = leaf;
+  return g;
+}
+
+int reduce_det_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int vbo,
+                      int nv, void *partial, int32_t *counter, bool zero_root) {
+  const bool nv1 = reduce_nv1(op, vbo, nv);
+  const DevPlan *d = &sf->dp;
+  if (reduce_dg(sf, op, nv)) {
+    DgArgs g = dg_args(sf, leaf, root);
+    g.zero_root = zero_root;
+    int rc;
+    // staged by bulk copies when both bases are 16-byte aligned, else direct loads
+    cudaError_t e = cudaErrorNotSupported;
+    if (sf->dp.n_dg_tiles > 0 && (reinterpret_cast<uintptr_t>(root) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(leaf) & 15) == 0) {
+      DgBulkArgs b{g, sf->dp.dg_tiles, sf->dp.n_dg_tiles, static_cast<int32_t *>(sf->status.p),
+                   sf->info.nroots_total * vbo, sf->info.leaf_extent_total * vbo};
+      e = launch_dg_bulk(u.dtype, op, vbo, b, s);
+    }
+    if (e == cudaErrorNotSupported) e = launch_dg(u.dtype, op, vbo, DgLaunch{&g, nullptr, nullptr, g.ntiles, g.ntiles, s});
+    if ((rc = launched(e))) return rc;
+    if (!sf->has_rest) return SF_SUCCESS;
+    d = &sf->dp_rest;   // the roots the chunks leave out
+  }
+  const RmTile *tiles = op == SF_REPLACE ? d->rm_winner_tiles : nv1 ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? d->n_rm_winner_tiles : nv1 ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
+  if (nt == 0) return SF_SUCCESS;
+  RmArgs a = rm_args_plan(sf, *d, tiles, nt, root, const_cast<void *>(leaf), nullptr, nv);
+  a.partial = partial;
+  a.counter = counter;
+  a.zero_root = zero_root;
+  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
+}
+
+// Zero the roots without leaves (and their argleaf entries, if given) for an operation that
+// starts its roots at zero.
+int zero_leafless(sf_t *sf, const sf_unit &u, void *root, int32_t *arg, cudaStream_t s) {
+  if (sf->dp.n_z_root == 0) return SF_SUCCESS;
   const int w = elem_size(u.dtype), ub = w * u.bs;
-  if (sf->info.nedges == 0) return SF_SUCCESS;
+  const int vb = pick_vb(w, ub, true, {root});
+  if (!vb) return SF_ERR_ALIGN;
+  return launched(launch_zero(vb, sf->dp.z_root, sf->dp.n_z_root, root, ub / vb, arg, u.bs, s));
+}
+
+int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s,
+                  bool from_zero = false) {
+  const int w = elem_size(u.dtype), ub = w * u.bs;
+  if (sf->info.nedges == 0) return from_zero ? zero_leafless(sf, u, root, nullptr, s) : SF_SUCCESS;
   if (reduce_atomic(sf, u.dtype, op)) {
+    // atomics combine into the roots in place: start them at zero first
+    if (from_zero && (sf->info.nroots_total > 0) &&
+        cudaMemsetAsync(root, 0, size_t(sf->info.nroots_total) * ub, s) != cudaSuccess)
+      return SF_ERR_CUDA;
     TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, leaf, root, nullptr, u.bs, PH_FUSED);
     return launched(launch_ts(u.dtype, op, w, true, true, false, a, sf->dp.n_ts_tiles, s));
   }
+  int rc;
+  if (from_zero && (rc = zero_leafless(sf, u, root, nullptr, s))) return rc;
   const int vb = pick_vb(w, ub, true, {root, leaf});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
   const int nv = ub / vbo;
-  int rc;
   if (op != SF_REPLACE && sf->dp.n_partial_slots > 0) {
+    // the full plan's scratch also serves the plan of the rest (a subset of its multi roots)
     const size_t pbytes = size_t(sf->dp.n_partial_slots) * nv * acc_pack_bytes(u.dtype, op, vbo);
     const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
     if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
   }
-  const bool nv1 = reduce_nv1(op, vbo, nv);
-  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
-  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
-  RmArgs a = rm_args(sf, tiles, nt, root, const_cast<void *>(leaf), nullptr, nv);
-  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
+  return reduce_det_launch(sf, u, leaf, root, op, s, vbo, nv, sf->partial.p, static_cast<int32_t *>(sf->counter.p),
+                           from_zero);
 }
 
 // ---- FetchAndOp ---------------------------------------------------------------------------
@@ -243,8 +307,11 @@ int reduce_mode(const sf_t *sf) { return sf->mode == SF_MODE_AUTO ? sf->tuned_mo
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op) {
   if (op == SF_REPLACE || dtype == SF_BF16) return false;
   if (reduce_mode(sf) == SF_MODE_ATOMIC) return true;
-  const bool float_sum = op == SF_SUM && (dtype == SF_FP32 || dtype == SF_FP64);
-  return !float_sum && sf->info.max_in_degree <= kOrderFreeMaxDegree;
+  // Only integer results are independent of the arrival order: a floating MIN/MAX keeps the
+  // first of two equal values (+0 and -0 compare equal), so it stays on the ordered fold.  A
+  // forest with diagonal chunks streams its roots faster than atomics reach them.
+  const bool integer = dtype == SF_INT32 || dtype == SF_INT64;
+  return integer && sf->info.max_in_degree <= kOrderFreeMaxDegree && sf->dp.dg_nchunks == 0;
 }
 
 int ensure_ready(const sf_t *sf) {
@@ -317,7 +384,15 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
                o_prr = b.add(h.pr_root), o_prl = b.add(h.pr_leaf), o_mro = b.add(h.m_root), o_mpt = b.add(h.m_ptr),
                o_mle = b.add(h.m_leaf), o_blk = b.add(h.block_recs), o_cmb = b.add(h.combs),
                o_rf = b.add(h.rm_fold_tiles), o_rf1 = b.add(h.rm_fold_nv1_tiles), o_rw = b.add(h.rm_winner_tiles),
-               o_rfe = b.add(h.rm_fetch_tiles);
+               o_rfe = b.add(h.rm_fetch_tiles), o_dgc = b.add(h.dg.chunks), o_dgx = b.add(h.dg.x),
+               o_dgl = b.add(h.dg.lists), o_z = b.add(h.z_root), o_dgt = b.add(h.dg.tiles);
+  // the root-major plan of the roots the diagonal chunks leave out (Reduce only)
+  static const HostPlan kNone;
+  const HostPlan &hr = h.rest ? *h.rest : kNone;
+  const size_t r_mask = b.add(hr.mask), r_prr = b.add(hr.pr_root), r_prl = b.add(hr.pr_leaf),
+               r_mro = b.add(hr.m_root), r_mpt = b.add(hr.m_ptr), r_mle = b.add(hr.m_leaf),
+               r_blk = b.add(hr.block_recs), r_cmb = b.add(hr.combs), r_rf = b.add(hr.rm_fold_tiles),
+               r_rf1 = b.add(hr.rm_fold_nv1_tiles), r_rw = b.add(hr.rm_winner_tiles);
   const size_t bytes = std::max<size_t>(b.host.size(), 256);
   if (cudaMalloc(&sf->blob.p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -361,6 +436,37 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.n_multi = int32_t(h.m_root.size());
   d.n_partial_slots = h.n_partial_slots;
   d.n_counters = h.n_counters;
+  d.dg_chunks = reinterpret_cast<const DiagChunk *>(base + o_dgc);
+  d.dg_x = reinterpret_cast<const int32_t *>(base + o_dgx);
+  d.dg_lists = reinterpret_cast<const int32_t *>(base + o_dgl);
+  d.dg_c0 = int32_t(h.dg.c0);
+  d.dg_nchunks = int32_t(h.dg.chunks.size());
+  d.z_root = reinterpret_cast<const int32_t *>(base + o_z);
+  d.n_z_root = int32_t(h.z_root.size());
+  d.dg_tiles = reinterpret_cast<const DgTile *>(base + o_dgt);
+  d.n_dg_tiles = int32_t(h.dg.tiles.size());
+  sf->has_rest = bool(h.rest);
+  {
+    DevPlan &r = sf->dp_rest;
+    r = DevPlan{};
+    r.mask = reinterpret_cast<const uint32_t *>(base + r_mask);
+    r.pr_root = reinterpret_cast<const int32_t *>(base + r_prr);
+    r.pr_leaf = reinterpret_cast<const int32_t *>(base + r_prl);
+    r.m_root = reinterpret_cast<const int32_t *>(base + r_mro);
+    r.m_ptr = reinterpret_cast<const int32_t *>(base + r_mpt);
+    r.m_leaf = reinterpret_cast<const int32_t *>(base + r_mle);
+    r.blocks = reinterpret_cast<const BlockRec *>(base + r_blk);
+    r.combs = reinterpret_cast<const Comb *>(base + r_cmb);
+    r.rm_fold_tiles = reinterpret_cast<const RmTile *>(base + r_rf);
+    r.rm_fold_nv1_tiles = reinterpret_cast<const RmTile *>(base + r_rf1);
+    r.rm_winner_tiles = reinterpret_cast<const RmTile *>(base + r_rw);
+    r.n_rm_fold_tiles = int32_t(hr.rm_fold_tiles.size());
+    r.n_rm_fold_nv1_tiles = int32_t(hr.rm_fold_nv1_tiles.size());
+    r.n_rm_winner_tiles = int32_t(hr.rm_winner_tiles.size());
+    r.n_multi = int32_t(hr.m_root.size());
+    r.n_partial_slots = hr.n_partial_slots;
+    r.n_counters = hr.n_counters;
+  }
   // fold scratch for units up to 16 bytes, so common operations allocate nothing later
   if ((rc = ensure(sf->partial, size_t(h.n_partial_slots) * 16, false, s)) ||
       (rc = ensure(sf->counter, size_t(h.n_counters) * 4 * 8, true, s)) || (rc = ensure(sf->status, 16, true, s)))
@@ -446,6 +552,39 @@ int sf_reduce_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, 
   if (!pd) return SF_ERR_NO_PENDING;
   drop_pending(sf, pd);
   return SF_SUCCESS;
+}
+
+int sf_reduce_from_zero_begin(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                              sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, op))) return rc;
+  const int w = elem_size(unit.dtype);
+  if ((sf->info.nroots_total && (rc = check_ptr(rootdata, w))) ||
+      (sf->info.leaf_extent_total && (rc = check_ptr(leafdata, w))))
+    return rc;
+  if (find_pending(sf, K_REDUCE_Z, unit, leafdata, rootdata, nullptr, op, 0, 0)) return SF_ERR_PENDING;
+  if ((rc = reduce_launch(sf, unit, leafdata, rootdata, op, static_cast<cudaStream_t>(stream), true))) return rc;
+  sf->pending.push_back(Pending{K_REDUCE_Z, unit, leafdata, rootdata, nullptr, op, 0, 0, 0});
+  return SF_SUCCESS;
+}
+
+int sf_reduce_from_zero_end(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdata, int32_t op,
+                            sf_stream_t stream) {
+  (void)stream;
+  if (!sf) return SF_ERR_NULL;
+  Pending *pd = find_pending(sf, K_REDUCE_Z, unit, leafdata, rootdata, nullptr, op, 0, 0);
+  if (!pd) return SF_ERR_NO_PENDING;
+  drop_pending(sf, pd);
+  return SF_SUCCESS;
+}
+
+int sf_zero_leafless_roots(sf_t *sf, sf_unit unit, void *rootdata, int32_t *argleaf, sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, SF_REPLACE))) return rc;
+  if (sf->info.nroots_total && ((rc = check_ptr(rootdata, elem_size(unit.dtype))) ||
+                                (argleaf && (rc = check_ptr(argleaf, 4)))))
+    return rc;
+  return zero_leafless(sf, unit, rootdata, argleaf, static_cast<cudaStream_t>(stream));
 }
 
 int sf_fetch_and_op_begin(sf_t *sf, sf_unit unit, void *rootdata, const void *leafdata, void *leafupdate, int32_t op,
@@ -732,11 +871,6 @@ extern "C" int sf_reduce_noalloc(sf_t *sf, sf_unit unit, const void *leafdata, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(scratch);
   if (cbytes && (rc = cuda_err(cudaMemsetAsync(base + coff, 0, cbytes, s)))) return rc;
-  const bool nv1 = reduce_nv1(op, vbo, nv);
-  const RmTile *tiles = op == SF_REPLACE ? sf->dp.rm_winner_tiles : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
-  const int nt = op == SF_REPLACE ? sf->dp.n_rm_winner_tiles : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
-  RmArgs a = rm_args(sf, tiles, nt, rootdata, const_cast<void *>(leafdata), nullptr, nv);
-  a.partial = base + poff;
-  a.counter = reinterpret_cast<int32_t *>(base + coff);
-  return launched(launch_rm(unit.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
+  return reduce_det_launch(sf, unit, leafdata, rootdata, op, s, vbo, nv, base + poff,
+                           reinterpret_cast<int32_t *>(base + coff));
 }

@@ -20,7 +20,7 @@ namespace {
 
 struct Group {
   int stage;
-  int family;   // 0 two-sided kernel, 1 root-major kernel
+  int family;   // 0 two-sided kernel, 1 root-major kernel, 2 diagonal-chunk Reduce
   int dtype, op, vb, mode;
   bool l2r, atomic;   // two-sided kernel; for the root-major kernel l2r marks one vector per unit
   size_t tiles_off;   // BatchTile offset in the tile table
@@ -39,9 +39,13 @@ bool same_ops(const std::vector<sf_batch_op> &a, const sf_batch_op *b, int32_t n
 struct sf_batch_s {
   std::vector<sf_batch_op> ops;    // the list the device tables were built for
   std::vector<int32_t> modes, paths;   // forests' resolved choices at build time
+  // every forest's fold scratch (partial, counter) as the tables captured it: a later
+  // operation on one of the forests may reallocate it, and the tables must then be rebuilt
+  std::vector<std::pair<const void *, const void *>> scratch;
   DevBuf tables;
   const TsArgs *ts_ops = nullptr;
   const RmArgs *rm_ops = nullptr;
+  const DgArgs *dg_ops = nullptr;
   const BatchTile *tiles = nullptr;
   std::vector<Group> groups;
   cudaGraph_t graph = nullptr;
@@ -62,6 +66,8 @@ void drop_graph(sf_batch_t *b) {
 int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
   std::vector<TsArgs> ts;
   std::vector<RmArgs> rm;
+  std::vector<int32_t> rm_src;   // the operation each RmArgs belongs to
+  std::vector<DgArgs> dg;
   std::vector<BatchTile> tiles;
   std::map<std::tuple<int, int, int, int, int, int, int, int>, std::vector<BatchTile>> grouped;
   std::vector<int32_t> modes(n, 0), paths(n, 0);
@@ -95,6 +101,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
         const int idx = int(rm.size());
         rm.push_back(rm_args(sf, sf->dp.rm_fold_tiles, sf->dp.n_rm_fold_tiles, const_cast<void *>(root),
                              const_cast<void *>(leaf), nullptr, ub / vbo));
+        rm_src.push_back(i);
         auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_BCAST, 0, 0}];
         for (int32_t t = 0; t < sf->dp.n_rm_fold_tiles; ++t) g.push_back(BatchTile{idx, 0, sf->dp.rm_fold_tiles + t});
       } else {   // fused (the three-phase path is not batched)
@@ -126,32 +133,37 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
           const size_t cbytes = size_t(sf->dp.n_counters) * nv * sizeof(int32_t);
           if ((rc = ensure(sf->partial, pbytes, false, s)) || (rc = ensure(sf->counter, cbytes, true, s))) return rc;
         }
+        // diagonal chunks first (their tiles by index), then the root-major plan of the rest
+        const DevPlan *d = &sf->dp;
+        if (reduce_dg(sf, o.op, nv)) {
+          const int idx = int(dg.size());
+          dg.push_back(dg_args(sf, leaf, const_cast<void *>(root)));
+          auto &g = grouped[{stage, 2, o.unit.dtype, o.op, vbo, 0, 0, 0}];
+          for (int32_t t = 0; t < dg.back().ntiles; ++t) g.push_back(BatchTile{idx, t, nullptr});
+          d = sf->has_rest ? &sf->dp_rest : nullptr;
+        }
         // one vector per unit: the group runs the Reduce kernel without the multi-vector fold,
         // on the forest's chunk tiles cut for it
         const bool nv1 = reduce_nv1(o.op, vbo, nv);
-        const RmTile *rt = o.op == SF_REPLACE ? sf->dp.rm_winner_tiles
-                                              : nv1 ? sf->dp.rm_fold_nv1_tiles : sf->dp.rm_fold_tiles;
-        const int nt = o.op == SF_REPLACE ? sf->dp.n_rm_winner_tiles
-                                          : nv1 ? sf->dp.n_rm_fold_nv1_tiles : sf->dp.n_rm_fold_tiles;
-        const int idx = int(rm.size());
-        rm.push_back(rm_args(sf, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
-        auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, int(nv1), 0}];
-        for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
+        const int nt = !d ? 0 : o.op == SF_REPLACE ? d->n_rm_winner_tiles
+                                                   : nv1 ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
+        if (nt > 0) {
+          const RmTile *rt = o.op == SF_REPLACE ? d->rm_winner_tiles : nv1 ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
+          const int idx = int(rm.size());
+          rm.push_back(rm_args_plan(sf, *d, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
+          rm_src.push_back(i);
+          auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, int(nv1), 0}];
+          for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
+        }
       }
     }
   }
   // rm_args captured the forests' scratch pointers before any ensure() above could move them:
   // refresh them now that every scratch buffer has its final size
-  for (int32_t i = 0, r = 0; i < n; ++i) {
-    const sf_batch_op &o = ops[i];
-    if (o.kind == SF_OP_BARRIER || o.sf->info.nedges == 0) continue;
-    const bool is_rm = (o.kind == SF_OP_BCAST && paths[i] == SF_PATH_ROOT_MAJOR) ||
-                       (o.kind == SF_OP_REDUCE && !reduce_atomic(o.sf, o.unit.dtype, o.op));
-    if (is_rm) {
-      rm[r].partial = o.sf->partial.p;
-      rm[r].counter = static_cast<int32_t *>(o.sf->counter.p);
-      ++r;
-    }
+  for (size_t r = 0; r < rm.size(); ++r) {
+    const sf_t *sf = ops[rm_src[r]].sf;
+    rm[r].partial = sf->partial.p;
+    rm[r].counter = static_cast<int32_t *>(sf->counter.p);
   }
   b->groups.clear();
   for (auto &kv : grouped) {
@@ -170,13 +182,15 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
     tiles.insert(tiles.end(), kv.second.begin(), kv.second.end());
     b->groups.push_back(g);
   }
-  // upload: [TsArgs][RmArgs][BatchTile], 256-byte aligned pieces
+  // upload: [TsArgs][RmArgs][DgArgs][BatchTile], 256-byte aligned pieces
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t o_ts = 0, o_rm = al(ts.size() * sizeof(TsArgs)), o_t = o_rm + al(rm.size() * sizeof(RmArgs));
+  const size_t o_ts = 0, o_rm = al(ts.size() * sizeof(TsArgs)), o_dg = o_rm + al(rm.size() * sizeof(RmArgs)),
+               o_t = o_dg + al(dg.size() * sizeof(DgArgs));
   const size_t bytes = std::max<size_t>(o_t + tiles.size() * sizeof(BatchTile), 256);
   std::vector<char> host(bytes, 0);
   if (!ts.empty()) memcpy(host.data() + o_ts, ts.data(), ts.size() * sizeof(TsArgs));
   if (!rm.empty()) memcpy(host.data() + o_rm, rm.data(), rm.size() * sizeof(RmArgs));
+  if (!dg.empty()) memcpy(host.data() + o_dg, dg.data(), dg.size() * sizeof(DgArgs));
   if (!tiles.empty()) memcpy(host.data() + o_t, tiles.data(), tiles.size() * sizeof(BatchTile));
   int rc;
   if (b->tables.bytes < bytes) {
@@ -189,10 +203,14 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
   char *base = static_cast<char *>(b->tables.p);
   b->ts_ops = reinterpret_cast<const TsArgs *>(base + o_ts);
   b->rm_ops = reinterpret_cast<const RmArgs *>(base + o_rm);
+  b->dg_ops = reinterpret_cast<const DgArgs *>(base + o_dg);
   b->tiles = reinterpret_cast<const BatchTile *>(base + o_t);
   b->ops.assign(ops, ops + n);
   b->modes = modes;
   b->paths = paths;
+  b->scratch.assign(n, {nullptr, nullptr});
+  for (int32_t i = 0; i < n; ++i)
+    if (ops[i].kind != SF_OP_BARRIER) b->scratch[i] = {ops[i].sf->partial.p, ops[i].sf->counter.p};
   return SF_SUCCESS;
 }
 
@@ -201,6 +219,8 @@ int launch_groups(sf_batch_t *b, cudaStream_t s) {
     cudaError_t e;
     if (g.family == 0)
       e = launch_ts(g.dtype, g.op, g.vb, g.l2r, g.atomic, false, TsLaunch{nullptr, b->ts_ops, b->tiles + g.tiles_off, g.ntiles, s});
+    else if (g.family == 2)
+      e = launch_dg(g.dtype, g.op, g.vb, DgLaunch{nullptr, b->dg_ops, b->tiles + g.tiles_off, g.ntiles, g.ntiles, s});
     else
       e = launch_rm(g.dtype, g.op, g.vb, g.mode,
                     RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.family == 1 && g.l2r != 0});
@@ -210,12 +230,14 @@ int launch_groups(sf_batch_t *b, cudaStream_t s) {
   return SF_SUCCESS;
 }
 
-// the forests' current choices differ from those the tables were built with
+// the forests' current choices or fold scratch differ from those the tables were built with
 bool choices_changed(const sf_batch_t *b) {
   for (size_t i = 0; i < b->ops.size(); ++i) {
     const sf_batch_op &o = b->ops[i];
+    if (o.kind == SF_OP_BARRIER) continue;
     if (o.kind == SF_OP_BCAST && bcast_path(o.sf) != b->paths[i]) return true;
     if (o.kind == SF_OP_REDUCE && reduce_mode(o.sf) != b->modes[i]) return true;
+    if (b->scratch[i].first != o.sf->partial.p || b->scratch[i].second != o.sf->counter.p) return true;
   }
   return false;
 }

@@ -1,6 +1,7 @@
 // sf_host.h -- host-side graph copy and plan construction (the setup pass, Sec. V.A-B).
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "sf.h"
@@ -20,6 +21,15 @@ struct Graph {
   int64_t E = 0;
 };
 
+// Diagonal chunks of the deterministic Reduce, on the host (sf_plan.h, DiagChunk).
+struct DiagHost {
+  std::vector<DiagChunk> chunks;
+  std::vector<int32_t> x, lists;
+  std::vector<DgTile> tiles;
+  int64_t c0 = 0;
+  int64_t roots = 0, extras = 0, list_roots = 0;
+};
+
 // Every plan array on the host, before upload.
 struct HostPlan {
   std::vector<Run> runs;
@@ -37,6 +47,10 @@ struct HostPlan {
   std::vector<Comb> combs;
   std::vector<RmTile> rm_fold_tiles, rm_fold_nv1_tiles, rm_winner_tiles, rm_fetch_tiles;
   int32_t n_partial_slots = 0, n_counters = 0;
+
+  std::vector<int32_t> z_root;      // roots without leaves (zeroed by the operations from zero)
+  DiagHost dg;                      // diagonal chunks (empty: none)
+  std::shared_ptr<HostPlan> rest;   // root-major plan of the roots the diagonal chunks leave out
 };
 
 // Validate and copy the arguments of sf_create.  Returns an SF_* code.

@@ -467,6 +467,7 @@ struct RmArgs {
   void *partial;        // scratch: fold partials of multi-block roots
   int32_t *counter;     // scratch: arrivals per (multi-block root, vector); zero between calls
   int32_t *status;      // device status word of the forest (DEVSTAT_* bits)
+  int32_t zero_root;    // Reduce from zero: every root counts as 0 before the operation (never read)
   int32_t nv;
   uint32_t nv_m;        // DivMagic of nv
   int32_t nv_s;
@@ -517,6 +518,17 @@ __device__ __forceinline__ bool stage2(void *dst0, const void *src0, uint32_t by
   if (threadIdx.x == 0 && status) atomicOr(status, DEVSTAT_STAGE_TIMEOUT);
   mbar_wait(b, 0, kWaitCycles);
   return false;
+}
+
+// The current value of root vector i for a Reduce: zero, without a load, when the operation
+// starts its roots at zero (sf_reduce_from_zero).
+template <typename T, int VB> __device__ __forceinline__ Pack<T, VB> ld_root(const void *root, int64_t i, bool zr) {
+  Pack<T, VB> z;
+  if (zr) {
+    memset(&z, 0, sizeof z);
+    return z;
+  }
+  return ld<T, VB>(root, i);
 }
 
 // Index load: read-only global path, or a plain load when the indices were staged in shared memory.
@@ -607,7 +619,7 @@ template <typename T, int VB, int OP>
 __device__ __forceinline__ void fold_finish(void *root, const Comb *combs, void *partial, int32_t *counter,
                                             int32_t nv, const Block &b, int32_t v,
                                             Pack<typename Acc<T, OP>::type, int(sizeof(typename Acc<T, OP>::type)) * Pack<T, VB>::L> acc,
-                                            Pack<T, VB> xr) {
+                                            Pack<T, VB> xr, bool zr) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
   const int64_t ri = int64_t(b.root) * nv + v;
@@ -639,7 +651,7 @@ __device__ __forceinline__ void fold_finish(void *root, const Comb *combs, void 
           finish = true;
         }
       }
-      if (finish) xr = ld<T, VB>(root, ri);
+      if (finish) xr = ld_root<T, VB>(root, ri, zr);
     }
   }
   if (finish) {
@@ -655,7 +667,7 @@ __device__ __forceinline__ void fold_finish(void *root, const Comb *combs, void 
 template <typename T, int VB, int OP, int MODE, bool SM = false>
 __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t *m_leaf, int32_t lofs,
                                            const Comb *combs, void *partial, int32_t *counter, int32_t nv,
-                                           const Block b, int32_t v) {
+                                           const Block b, int32_t v, bool zr = false) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
   constexpr int U = VB >= 16 ? 2 : 4;
@@ -684,7 +696,7 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
   } else if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE) {
     // left fold of this block in canonical order, U leaves in flight
     Pack<T, VB> xr;
-    if (b.comb < 0) xr = ld<T, VB>(root, ri);   // issued early: independent of the fold
+    if (b.comb < 0) xr = ld_root<T, VB>(root, ri, zr);   // issued early: independent of the fold
     Pack<A, AVB> acc;
     int32_t e = 0;
     {
@@ -712,7 +724,7 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
 #pragma unroll
           for (int l = 0; l < Pack<T, VB>::L; ++l) acc.v[l] = combine<OP, A>(acc.v[l], to_acc<A, T>(y[u].v[l]));
     }
-    fold_finish<T, VB, OP>(root, combs, partial, counter, nv, b, v, acc, xr);
+    fold_finish<T, VB, OP>(root, combs, partial, counter, nv, b, v, acc, xr, zr);
   }
 }
 
@@ -748,7 +760,7 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
 #pragma unroll
   for (int j = 0; j < NBT; ++j) {
     const int32_t w = threadIdx.x + j * kThreads;
-    if (w < t.cnt && rec[w].who >= 0) xr[j] = ld<T, VB>(a.root, rec[w].who);   // single-block root
+    if (w < t.cnt && rec[w].who >= 0) xr[j] = ld_root<T, VB>(a.root, rec[w].who, a.zero_root);   // single-block root
   }
   for (int32_t q0 = 0; q0 < nE; q0 += R) {
     const int32_t nq = min(R, nE - q0);
@@ -776,7 +788,7 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
     const int32_t w = threadIdx.x + j * kThreads;
     if (w < t.cnt) {
       const Block b = load_block(rec, a.combs, w);
-      fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, 1, b, 0, acc[j], xr[j]);
+      fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, 1, b, 0, acc[j], xr[j], a.zero_root);
     }
   }
 }
@@ -786,7 +798,7 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
 // independent load chains going; each root still folds its leaves in canonical order.
 template <typename T, int VB, int OP, int NB, bool SM = false>
 __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t *m_leaf, int32_t lofs, int32_t nv,
-                                          const Block (&b)[NB], const int32_t (&v)[NB]) {
+                                          const Block (&b)[NB], const int32_t (&v)[NB], bool zr) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
   constexpr int U = VB >= 16 ? 1 : 2;
@@ -795,7 +807,7 @@ __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t 
   int32_t nmax = 0;
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
-    x[j] = ld<T, VB>(root, int64_t(b[j].root) * nv + v[j]);
+    x[j] = ld_root<T, VB>(root, int64_t(b[j].root) * nv + v[j], zr);
     nmax = b[j].n > nmax ? b[j].n : nmax;
   }
   for (int32_t e = 0; e < nmax; e += U) {
@@ -858,7 +870,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
         mk[u] = 0;
         if (k < t.cnt) {
           mk[u] = (__ldg(mw + (k >> 5)) >> (k & 31)) & 1u;
-          if constexpr (need_root) x[u] = ld<T, VB>(rbase, k);
+          if constexpr (need_root) x[u] = ld_root<T, VB>(rbase, k, MODE == RM_REDUCE && a.zero_root);
           if constexpr (need_leaf) y[u] = ld<T, VB>(lbase, k);
         }
       }
@@ -907,7 +919,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (on[u]) {
-          if constexpr (SingleReads<OP, MODE>::root) x[u] = ld<T, VB>(a.root, ri[u]);
+          if constexpr (SingleReads<OP, MODE>::root) x[u] = ld_root<T, VB>(a.root, ri[u], MODE == RM_REDUCE && a.zero_root);
           if constexpr (SingleReads<OP, MODE>::leaf) y[u] = ld<T, VB>(a.leaf, li[u]);
         }
 #pragma unroll
@@ -978,25 +990,25 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
             simple &= b[j].comb < 0;
           }
           if (simple) {
-            fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v);
+            fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v, a.zero_root);
           } else {
   #pragma unroll
             for (int j = 0; j < NB; ++j)
               fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv, b[j],
-                                                v[j]);
+                                                v[j], a.zero_root);
           }
         }
         for (; w < work; w += kThreads) {
           const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
           fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
-                                            load_block(s_rec, a.combs, t.a + cl - r0), v);
+                                            load_block(s_rec, a.combs, t.a + cl - r0), v, a.zero_root);
         }
       }
     } else {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
         const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
         fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, 0, a.combs, a.partial, a.counter, nv,
-                                    load_block(a.blocks, a.combs, t.a + cl), v);
+                                    load_block(a.blocks, a.combs, t.a + cl), v, a.zero_root);
       }
     }
   }
@@ -1007,6 +1019,403 @@ __global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP,
     rm_kernel(RmArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
   rm_tile<T, VB, OP, MODE, NV1>(a, t);
+}
+
+// ------------------------------------------------------------------ diagonal-chunk Reduce
+// Deterministic Reduce (SUM/MIN/MAX) of one-vector units over the diagonal chunks (sf_plan.h):
+// a warp takes 32 consecutive roots, lane l root 32 (c0 + c) + l, and U chunks at a time.  Per
+// chunk the loads come in three dependent rounds, each a coalesced or broadcast access:
+//   1. the 16-byte chunk record (every lane the same address) and the root vectors;
+//   2. the diagonal leaves (root + delta) and, for roots with other leaves, their x entries
+//      (the i-th such root of the chunk reads x[xoff + i]: a ballot and a popcount);
+//   3. the other leaf of DG_PAIR roots.
+// Each root then folds its leaves in canonical order (the diagonal leaf in its place) and
+// stores root op= fold: with at most DG_MAX_LEAVES leaves, D is the plain left fold.  DG_LIST
+// roots (three or more leaves) are rare and read their list one lane at a time.
+struct DgArgs {
+  const DiagChunk *chunks;
+  const int32_t *x, *lists;
+  int32_t c0, nchunks;   // chunk c of the plan covers root units 32 (c0 + c) .. + 31
+  int32_t nroots;        // root units of the forest (a last chunk may run past them)
+  int32_t ntiles;        // DG_TILE_CHUNKS chunks per tile
+  int32_t zero_root;     // Reduce from zero: roots count as 0 (never read)
+  void *root;
+  const void *leaf;
+};
+constexpr int DG_WARP_CHUNKS = 4;                         // chunks per warp per tile
+static_assert(DG_WARP_CHUNKS * (kThreads / 32) == DG_TILE_CHUNKS, "a tile is one chunk group per warp");
+// chunks in flight per warp: four, one for 16-byte units (their packs fill 64 registers)
+template <int VB> struct DgUnroll { static constexpr int value = VB >= 16 ? 1 : 4; };
+
+// A DG_LIST root u (rare): its list at lists[o] -- header -1 - (leaves before | after << 16),
+// then the other leaves -- folded with the diagonal leaf u + delta in its canonical place.
+template <typename T, int VB, int OP>
+__device__ __forceinline__ void dg_list_root(const DgArgs &a, int64_t u, int32_t o, int32_t delta) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  const int32_t h = -1 - __ldg(a.lists + o);
+  const int32_t nb = h & 0xffff, n = nb + 1 + (h >> 16);
+  Pack<A, AVB> acc;
+  for (int32_t i = 0; i < n; ++i) {
+    const int64_t lu = i == nb ? u + delta : int64_t(__ldg(a.lists + o + 1 + (i < nb ? i : i - 1)));
+    const Pack<T, VB> y = ld<T, VB>(a.leaf, lu);
+#pragma unroll
+    for (int l = 0; l < Pack<T, VB>::L; ++l)
+      acc.v[l] = i == 0 ? to_acc<A, T>(y.v[l]) : combine<OP, A>(acc.v[l], to_acc<A, T>(y.v[l]));
+  }
+  Pack<T, VB> xr = ld_root<T, VB>(a.root, u, a.zero_root);
+#pragma unroll
+  for (int l = 0; l < Pack<T, VB>::L; ++l) xr.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
+  st<T, VB>(a.root, u, xr);
+}
+
+template <typename T, int VB, int OP>
+__device__ __forceinline__ void dg_tile(const DgArgs &a, int32_t tile) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  const int lane = threadIdx.x & 31;
+  const uint32_t below = (1u << lane) - 1u;
+  constexpr int DG_U = DgUnroll<VB>::value;
+  const int32_t cw = tile * DG_TILE_CHUNKS + (threadIdx.x >> 5) * DG_WARP_CHUNKS;
+  for (int32_t cb = cw; cb < cw + DG_WARP_CHUNKS && cb < a.nchunks; cb += DG_U) {
+    uint32_t code[DG_U];
+    int32_t xo[DG_U], dl[DG_U];
+    Pack<T, VB> xr[DG_U], yd[DG_U], yo[DG_U];
+#pragma unroll
+    for (int j = 0; j < DG_U; ++j) {   // round 1: chunk records and roots
+      code[j] = 0;
+      const int32_t c = cb + j;
+      if (c < a.nchunks) {
+        const uint4 rec = __ldg(reinterpret_cast<const uint4 *>(a.chunks) + c);
+        code[j] = ((lane < 16 ? rec.x : rec.y) >> (2 * (lane & 15))) & 3u;
+        xo[j] = int32_t(rec.z);
+        dl[j] = int32_t(rec.w);
+        const int64_t u = int64_t(a.c0 + c) * 32 + lane;
+        if (u < a.nroots) xr[j] = ld_root<T, VB>(a.root, u, a.zero_root);
+      }
+    }
+    int32_t xe[DG_U];
+#pragma unroll
+    for (int j = 0; j < DG_U; ++j) {   // round 2: diagonal leaves and x entries
+      const int64_t u = int64_t(a.c0 + cb + j) * 32 + lane;
+      const uint32_t more = __ballot_sync(0xffffffffu, code[j] >= DG_PAIR);
+      xe[j] = 0;
+      if (code[j] != DG_SKIP) yd[j] = ld<T, VB>(a.leaf, u + dl[j]);
+      if (code[j] >= DG_PAIR) xe[j] = __ldg(a.x + xo[j] + __popc(more & below));
+    }
+#pragma unroll
+    for (int j = 0; j < DG_U; ++j)     // round 3: the other leaf of two-leaf roots
+      if (code[j] == DG_PAIR) yo[j] = ld<T, VB>(a.leaf, xe[j] & 0x7fffffff);
+#pragma unroll
+    for (int j = 0; j < DG_U; ++j) {
+      const int64_t u = int64_t(a.c0 + cb + j) * 32 + lane;
+      if (code[j] == DG_DIAG || code[j] == DG_PAIR) {
+        // canonical order: the other leaf first unless its entry has the top bit (after)
+        const bool pair = code[j] == DG_PAIR, after = xe[j] < 0;
+        const Pack<T, VB> &y0 = pair && !after ? yo[j] : yd[j];
+        Pack<T, VB> r = xr[j];
+#pragma unroll
+        for (int l = 0; l < Pack<T, VB>::L; ++l) {
+          A acc = to_acc<A, T>(y0.v[l]);
+          if (pair) acc = combine<OP, A>(acc, to_acc<A, T>(after ? yo[j].v[l] : yd[j].v[l]));
+          r.v[l] = apply_acc<OP, T, A>(xr[j].v[l], acc);
+        }
+        st<T, VB>(a.root, u, r);
+      }
+    }
+    // roots of three or more leaves, after the others (their root and diagonal leaf are
+    // read again, from L1 or L2, so that little stays live here)
+#pragma unroll
+    for (int j = 0; j < DG_U; ++j)
+      if (code[j] == DG_LIST) dg_list_root<T, VB, OP>(a, int64_t(a.c0 + cb + j) * 32 + lane, xe[j], dl[j]);
+  }
+}
+
+template <typename T, int VB, int OP>
+__global__ void __launch_bounds__(kThreads, 4) dg_kernel(DgArgs a) {
+  for (int32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) dg_tile<T, VB, OP>(a, t);
+}
+
+// ------------------------------------------------------------------ staged diagonal-chunk Reduce
+// The same Reduce as dg_kernel, for one forest, with its tiles staged in shared memory by the
+// bulk-copy engine: a persistent CTA loops over the plan's tiles (DgTile: up to 64 chunks of one
+// delta) and keeps two stages, so the next tile's copies are in flight while it folds this one.
+// Per tile, thread 0 issues up to four cp.async.bulk copies on the stage's mbarrier -- the
+// roots (unless the Reduce starts from zero), the diagonal leaves (the span widened to 16-byte
+// boundaries inside the leaf array), the chunk records and the tile's x entries -- so every
+// byte the tile must read except the other leaves of two-leaf roots (a gather, 15% of the roots
+// of the SpMV scatter) arrives in one round.  A tile whose roots are all in the plan writes them
+// back with one bulk store; others store root by root.  Units outside a copied span (the ends of
+// the arrays) are read and written directly.  Base pointers must be 16-byte aligned.
+struct DgBulkArgs {
+  DgArgs a;
+  const DgTile *tiles;
+  int32_t ntiles;
+  int32_t *status;        // forest status word (a bulk copy that did not land)
+  int64_t root_bytes;     // bytes of the root and leaf arrays (spans are clamped inside them)
+  int64_t leaf_bytes;
+};
+
+// Shared-memory stage of one tile of VB-byte units: roots, diagonal leaves, chunk records, x
+// entries, list entries, and the gathered leaf values of the lists.  Widening a span to 16-byte
+// boundaries adds less than 16 bytes at each end, so the leaf, x and list areas have 32 bytes to
+// spare.
+template <int VB> struct DgStage {
+  static constexpr int R = DG_TILE_CHUNKS * 32 * VB;
+  static constexpr int O_LEAF = R;
+  static constexpr int O_REC = O_LEAF + R + 32;
+  static constexpr int O_X = O_REC + DG_TILE_CHUNKS * 16;
+  static constexpr int O_L = O_X + DG_TILE_XCAP * 4 + 32;
+  static constexpr int O_LV = O_L + DG_TILE_LCAP * 4 + 32;
+  static constexpr int BYTES = (O_LV + DG_TILE_LCAP * VB + 127) / 128 * 128;
+};
+
+// One bulk copy global -> shared on mbarrier `bar` (sizes multiples of 16, both addresses
+// 16-byte aligned); the copy is counted in the barrier's expected bytes by the caller.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// The spans a tile stages (bytes, relative to each array's base).
+struct DgSpans {
+  int64_t u0, L0;          // first root unit, its diagonal leaf unit
+  int32_t n;               // roots of the tile (below the forest's last root)
+  int32_t rstage;          // root bytes staged (and stored back whole), a multiple of 16
+  int64_t llo, lhi;        // leaf bytes [llo, lhi) staged
+  int64_t xlo, xhi;        // x-entry bytes [xlo, xhi) staged
+  int64_t lslo, lshi;      // list-entry bytes [lslo, lshi) staged (empty: lists read from global)
+};
+template <int VB>
+__device__ __forceinline__ DgSpans dg_spans(const DgBulkArgs &b, const DgTile &t) {
+  DgSpans p;
+  p.u0 = int64_t(b.a.c0 + t.c) * 32;
+  p.n = int32_t(min(int64_t(t.n) * 32, int64_t(b.a.nroots) - p.u0));
+  p.rstage = (p.n * VB) & ~15;
+  p.L0 = p.u0 + t.delta;
+  p.llo = max(int64_t(0), (p.L0 * VB) & ~int64_t(15));   // inside the leaf array: the tile's first
+                                                            // root need not have its diagonal leaf
+  p.lhi = min(((p.L0 + p.n) * VB + 15) & ~int64_t(15), b.leaf_bytes & ~int64_t(15));
+  if (p.lhi < p.llo) p.lhi = p.llo;
+  p.xlo = (int64_t(t.xbeg) * 4) & ~int64_t(15);
+  p.xhi = (int64_t(t.xend) * 4 + 15) & ~int64_t(15);
+  if (t.xend == t.xbeg) p.xhi = p.xlo;
+  p.lslo = (int64_t(t.lbeg) * 4) & ~int64_t(15);
+  p.lshi = (int64_t(t.lend) * 4 + 15) & ~int64_t(15);
+  if (t.lend == t.lbeg || t.lend - t.lbeg > DG_TILE_LCAP) p.lshi = p.lslo;
+  return p;
+}
+
+template <typename T, int VB>
+__device__ __forceinline__ void dg_issue(const DgBulkArgs &b, unsigned char *sg, uint32_t bar, int32_t t) {
+  using S = DgStage<VB>;
+  const DgTile tl = b.tiles[t];
+  const DgSpans p = dg_spans<VB>(b, tl);
+  const uint32_t rb = b.a.zero_root ? 0u : uint32_t(p.rstage);
+  const uint32_t lb = uint32_t(p.lhi - p.llo), cb = uint32_t(tl.n) * 16u, xb = uint32_t(p.xhi - p.xlo);
+  const uint32_t sb = uint32_t(p.lshi - p.lslo);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(rb + lb + cb + xb + sb)
+               : "memory");
+  if (rb) bulk_load(sg, static_cast<const char *>(b.a.root) + p.u0 * VB, rb, bar);
+  if (lb) bulk_load(sg + S::O_LEAF, static_cast<const char *>(b.a.leaf) + p.llo, lb, bar);
+  bulk_load(sg + S::O_REC, b.a.chunks + tl.c, cb, bar);
+  if (xb) bulk_load(sg + S::O_X, reinterpret_cast<const char *>(b.a.x) + p.xlo, xb, bar);
+  if (sb) bulk_load(sg + S::O_L, reinterpret_cast<const char *>(b.a.lists) + p.lslo, sb, bar);
+}
+
+// Fold one staged tile; the results of a full tile go back into the stage's root area.  FAST:
+// the tile's roots and diagonal leaves are staged whole (no array end inside the tile), so
+// every root and diagonal leaf is read from shared memory at a fixed offset, in 32 bits.
+template <typename T, int VB, int OP, bool FAST>
+__device__ __forceinline__ void dg_fold_stage(const DgBulkArgs &b, unsigned char *sg, const DgTile &tl,
+                                              const DgSpans &p) {
+  using A = typename Acc<T, OP>::type;
+  using S = DgStage<VB>;
+  using P = Pack<T, VB>;
+  const DgArgs &a = b.a;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t below = (1u << lane) - 1u;
+  const int sh = 2 * (lane & 15);
+  const bool hi = lane >= 16;
+  const int32_t *xs = reinterpret_cast<const int32_t *>(sg + S::O_X) - p.xlo / 4;   // xs[e]: x entry e
+  const bool zr = a.zero_root, whole = tl.full;
+  const uint32_t lofs = FAST ? uint32_t(S::O_LEAF + (p.L0 * VB - p.llo)) : 0u;   // diagonal leaf 0 in the stage
+  auto root_ld = [&](int32_t i) -> P {
+    if (FAST) {
+      if (zr) return ld_root<T, VB>(nullptr, 0, true);
+      return *reinterpret_cast<const P *>(sg + i * VB);
+    }
+    if (!zr && i * VB < p.rstage) return *reinterpret_cast<const P *>(sg + i * VB);
+    return ld_root<T, VB>(a.root, p.u0 + i, zr);
+  };
+  auto leaf_ld = [&](int32_t i) -> P {
+    if (FAST) return *reinterpret_cast<const P *>(sg + lofs + uint32_t(i) * VB);
+    const int64_t gb = (p.L0 + i) * VB;
+    if (gb >= p.llo && gb + VB <= p.lhi) return *reinterpret_cast<const P *>(sg + S::O_LEAF + (gb - p.llo));
+    return ld<T, VB>(a.leaf, p.L0 + i);
+  };
+  auto root_st = [&](int32_t i, const P &r) {
+    if (FAST ? whole : whole && i * VB < p.rstage) *reinterpret_cast<P *>(sg + i * VB) = r;
+    else st<T, VB>(a.root, p.u0 + i, r);
+  };
+  // the leaf values of the tile's lists (staged list entries >= 0; headers are negative),
+  // gathered by the whole CTA into shared memory with cp.async, awaited before the fold
+  const bool lstaged = p.lshi > p.lslo;
+  const int32_t *sl = reinterpret_cast<const int32_t *>(sg + S::O_L) - p.lslo / 4;   // sl[o]: list entry o
+  P *slv = reinterpret_cast<P *>(sg + S::O_LV) - tl.lbeg;                             // slv[o]: its leaf value
+  if (lstaged)
+    for (int32_t o = tl.lbeg + int32_t(threadIdx.x); o < tl.lend; o += kThreads) {
+      const int32_t e = sl[o];
+      if (e >= 0) cp_async_vec<VB>(slv + o, static_cast<const char *>(a.leaf) + int64_t(e) * VB);
+    }
+  constexpr int J = DG_WARP_CHUNKS;
+  uint32_t code[J];
+  int32_t xe[J];
+  P xr[J], yd[J], yo[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {   // staged values, and the gathers of the other leaves
+    const int32_t cc = warp * J + j, i = cc * 32 + lane;
+    code[j] = 0;
+    xe[j] = 0;
+    if (cc < tl.n) {
+      const uint4 rec = *reinterpret_cast<const uint4 *>(sg + S::O_REC + cc * 16);
+      code[j] = ((hi ? rec.y : rec.x) >> sh) & 3u;
+      const uint32_t more = __ballot_sync(0xffffffffu, code[j] >= DG_PAIR);
+      if (code[j] >= DG_PAIR) xe[j] = xs[int32_t(rec.z) + __popc(more & below)];
+      if (code[j] != DG_SKIP) {
+        xr[j] = root_ld(i);
+        yd[j] = leaf_ld(i);
+      }
+      if (code[j] == DG_PAIR) yo[j] = ld<T, VB>(a.leaf, xe[j] & 0x7fffffff);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int32_t i = (warp * J + j) * 32 + lane;
+    if (code[j] == DG_DIAG || code[j] == DG_PAIR) {
+      const bool pair = code[j] == DG_PAIR, after = xe[j] < 0;
+      const P &y0 = pair && !after ? yo[j] : yd[j];
+      P r = xr[j];
+#pragma unroll
+      for (int l = 0; l < P::L; ++l) {
+        A acc = to_acc<A, T>(y0.v[l]);
+        if (pair) acc = combine<OP, A>(acc, to_acc<A, T>(after ? yo[j].v[l] : yd[j].v[l]));
+        r.v[l] = apply_acc<OP, T, A>(xr[j].v[l], acc);
+      }
+      root_st(i, r);
+    } else if (code[j] == DG_LIST) {
+      // three or more leaves: the list (header, then the other leaves) and its gathered values
+      // in shared memory, or from global memory for a tile whose lists did not fit the stage
+      const int32_t o = xe[j], h = -1 - (lstaged ? sl[o] : __ldg(a.lists + o));
+      const int32_t nb = h & 0xffff, nl = nb + 1 + (h >> 16);
+      Pack<A, int(sizeof(A)) * P::L> acc;
+      for (int32_t k = 0; k < nl; ++k) {
+        const int32_t ok = o + 1 + (k < nb ? k : k - 1);
+        const P y = k == nb ? yd[j] : lstaged ? slv[ok] : ld<T, VB>(a.leaf, __ldg(a.lists + ok));
+#pragma unroll
+        for (int l = 0; l < P::L; ++l)
+          acc.v[l] = k == 0 ? to_acc<A, T>(y.v[l]) : combine<OP, A>(acc.v[l], to_acc<A, T>(y.v[l]));
+      }
+      P r = xr[j];
+#pragma unroll
+      for (int l = 0; l < P::L; ++l) r.v[l] = apply_acc<OP, T, A>(xr[j].v[l], acc.v[l]);
+      root_st(i, r);
+    }
+  }
+}
+
+// A tile at an end of the root or leaf array (rare): out of line, so that the common path keeps
+// its registers.
+template <typename T, int VB, int OP>
+__device__ __noinline__ void dg_fold_edge(const DgBulkArgs &b, unsigned char *sg, const DgTile &tl, const DgSpans &p) {
+  dg_fold_stage<T, VB, OP, false>(b, sg, tl, p);
+}
+
+// Four CTAs per SM for units up to 8 bytes (two stages of 27 KB for 8-byte units, 64 registers);
+// 16-byte units fit two.
+template <typename T, int VB, int OP>
+__global__ void __launch_bounds__(kThreads, VB >= 16 ? 2 : 3) dg_bulk_kernel(DgBulkArgs b) {
+  using S = DgStage<VB>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ alignas(8) uint64_t bar[2];
+  const uint32_t b0 = smem_addr(&bar[0]), b1 = smem_addr(&bar[1]);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int32_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (int32_t(blockIdx.x) < b.ntiles) dg_issue<T, VB>(b, dsm, b0, blockIdx.x);
+    if (int32_t(blockIdx.x) + G < b.ntiles) dg_issue<T, VB>(b, dsm + S::BYTES, b1, blockIdx.x + G);
+  }
+  uint32_t phase = 0;   // bit s: the parity stage s waits for next
+  int32_t i = 0;
+  for (int32_t t = blockIdx.x; t < b.ntiles; t += G, ++i) {
+    const int s = i & 1;
+    unsigned char *sg = dsm + s * S::BYTES;
+    const uint32_t bs = s ? b1 : b0;
+    const bool ok = mbar_wait(bs, (phase >> s) & 1u, kWaitCycles);
+    if (!__syncthreads_and(ok)) {
+      // a copy did not land: record it, let this tile's and the other stage's copies finish
+      // (bounded), wait for the stores, and stop
+      if (threadIdx.x == 0) {
+        if (b.status) atomicOr(b.status, DEVSTAT_STAGE_TIMEOUT);
+        mbar_wait(bs, (phase >> s) & 1u, kWaitCycles);
+        if (t + G < b.ntiles) mbar_wait(s ? b0 : b1, (phase >> (s ^ 1)) & 1u, kWaitCycles);
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      }
+      return;
+    }
+    phase ^= 1u << s;
+    const DgTile tl = b.tiles[t];
+    const DgSpans p = dg_spans<VB>(b, tl);
+    if (p.rstage == p.n * VB && p.llo <= p.L0 * VB && p.lhi >= (p.L0 + p.n) * VB)
+      dg_fold_stage<T, VB, OP, true>(b, sg, tl, p);
+    else
+      dg_fold_edge<T, VB, OP>(b, sg, tl, p);
+    // the folded roots of a full tile leave by one bulk store; then the stage takes tile t + 2G
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (tl.full && p.rstage > 0) {
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                     ::"l"(static_cast<char *>(b.a.root) + p.u0 * VB), "r"(smem_addr(sg)), "r"(uint32_t(p.rstage))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      }
+      if (t + 2 * G < b.ntiles) dg_issue<T, VB>(b, sg, bs, t + 2 * G);
+    }
+  }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ roots without leaves
+// Zero the listed units (roots without leaves, for the operations that start their roots at
+// zero): `units` holds unit indices, each nv vectors of VB bytes; with `arg`, the unit's bs
+// entries of arg are set to -1 as well.
+template <int VB>
+__global__ void __launch_bounds__(kThreads) zero_units_kernel(const int32_t *units, int32_t n, void *data, int32_t nv,
+                                                              int32_t *arg, int32_t bs) {
+  using R = typename Raw<VB>::type;
+  const int64_t work = int64_t(n) * nv;
+  for (int64_t w = blockIdx.x * int64_t(kThreads) + threadIdx.x; w < work; w += int64_t(gridDim.x) * kThreads) {
+    const int64_t k = w / nv, v = w - k * nv;
+    R z;
+    memset(&z, 0, sizeof z);
+    reinterpret_cast<R *>(data)[int64_t(units[k]) * nv + v] = z;
+  }
+  if (arg) {
+    const int64_t na = int64_t(n) * bs;
+    for (int64_t w = blockIdx.x * int64_t(kThreads) + threadIdx.x; w < na; w += int64_t(gridDim.x) * kThreads) {
+      const int64_t k = w / bs;
+      arg[int64_t(units[k]) * bs + (w - k * bs)] = -1;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ MAX with location
@@ -1116,7 +1525,7 @@ __global__ void __launch_bounds__(kThreads) maxloc_scatter_kernel(const int32_t 
 // entry points at the tile itself, so the arguments and the tile load side by side.
 struct BatchTile {
   int32_t op;          // index into the operation table
-  int32_t pad;
+  int32_t pad;         // the tile index of a diagonal-chunk operation (its `tile` is unused)
   const void *tile;    // TsTile or RmTile of that operation's forest (device address)
 };
 
@@ -1136,6 +1545,12 @@ __global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP,
   const RmArgs a = ops[bt.op];
   const RmTile t = *static_cast<const RmTile *>(bt.tile);
   rm_tile<T, VB, OP, MODE, NV1>(a, t);
+}
+
+template <typename T, int VB, int OP>
+__global__ void __launch_bounds__(kThreads, 4) dg_batch_kernel(const DgArgs *ops, const BatchTile *tiles) {
+  const BatchTile bt = tiles[blockIdx.x];
+  dg_tile<T, VB, OP>(ops[bt.op], bt.pad);
 }
 
 }  // namespace sfgb

@@ -1,4 +1,6 @@
 // sf_launch.cu -- runtime dispatch to the kernel instantiations; raw-copy (REPLACE) kernels.
+#include <algorithm>
+
 #include "sf.h"
 #include "sf_launch_impl.cuh"
 
@@ -71,6 +73,43 @@ cudaError_t launch_rm(int dtype, int op, int vb, int mode, const RmLaunch &L) {
     case SF_FP32: return launch_rm_t<float>(op, vb, mode, L);
     case SF_FP64: return launch_rm_t<double>(op, vb, mode, L);
     case SF_BF16: return launch_rm_t<bf16>(op, vb, mode, L);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_zero(int vb, const int32_t *units, int32_t n, void *data, int32_t nv, int32_t *arg, int32_t bs,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t work = int64_t(n) * (nv > bs ? nv : bs);
+  const int grid = int(std::min<int64_t>((work + kThreads - 1) / kThreads, 152 * 16));
+  switch (vb) {
+    case 2: zero_units_kernel<2><<<grid, kThreads, 0, s>>>(units, n, data, nv, arg, bs); break;
+    case 4: zero_units_kernel<4><<<grid, kThreads, 0, s>>>(units, n, data, nv, arg, bs); break;
+    case 8: zero_units_kernel<8><<<grid, kThreads, 0, s>>>(units, n, data, nv, arg, bs); break;
+    case 16: zero_units_kernel<16><<<grid, kThreads, 0, s>>>(units, n, data, nv, arg, bs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dg(int dtype, int op, int vb, const DgLaunch &L) {
+  switch (dtype) {
+    case SF_INT32: return launch_dg_t<int32_t>(op, vb, L);
+    case SF_INT64: return launch_dg_t<int64_t>(op, vb, L);
+    case SF_FP32: return launch_dg_t<float>(op, vb, L);
+    case SF_FP64: return launch_dg_t<double>(op, vb, L);
+    case SF_BF16: return launch_dg_t<bf16>(op, vb, L);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dg_bulk(int dtype, int op, int vb, const DgBulkArgs &b, cudaStream_t s) {
+  switch (dtype) {
+    case SF_INT32: return launch_dg_bulk_t<int32_t>(op, vb, b, s);
+    case SF_INT64: return launch_dg_bulk_t<int64_t>(op, vb, b, s);
+    case SF_FP32: return launch_dg_bulk_t<float>(op, vb, b, s);
+    case SF_FP64: return launch_dg_bulk_t<double>(op, vb, b, s);
+    case SF_BF16: return launch_dg_bulk_t<bf16>(op, vb, b, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -98,6 +98,77 @@ cudaError_t launch_ts_ops_t(int op, int vb, bool atomic, bool fetch, const TsLau
   return cudaErrorInvalidValue;
 }
 
+template <typename T, int VB, int OP>
+cudaError_t go_dg(const DgLaunch &L) {
+  if (L.ntiles <= 0) return cudaSuccess;
+  if (L.tiles) dg_batch_kernel<T, VB, OP><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+  else dg_kernel<T, VB, OP><<<L.grid, kThreads, 0, L.s>>>(*L.single);
+  return cudaGetLastError();
+}
+
+// The staged kernel: a persistent grid of as many CTAs as fit the GPU (two stages of
+// DgStage<VB> in dynamic shared memory each).  cudaErrorNotSupported when it cannot be set up.
+template <typename T, int VB, int OP>
+cudaError_t go_dg_bulk(const DgBulkArgs &b, cudaStream_t s) {
+  if (b.ntiles <= 0) return cudaSuccess;
+  constexpr int smem = 2 * DgStage<VB>::BYTES;
+  static const int per_sm = [] {
+    int n = 0;
+    if (cudaFuncSetAttribute(dg_bulk_kernel<T, VB, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dg_bulk_kernel<T, VB, OP>, kThreads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  }();
+  int dev = 0, sms = 0;
+  if (per_sm <= 0 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  const int grid = b.ntiles < per_sm * sms ? b.ntiles : per_sm * sms;
+  dg_bulk_kernel<T, VB, OP><<<grid, kThreads, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+template <typename T, int VB>
+static cudaError_t dg_bulk_op(int op, const DgBulkArgs &b, cudaStream_t s) {
+  switch (op) {
+    case OP_SUM: return go_dg_bulk<T, VB, OP_SUM>(b, s);
+    case OP_MIN: return go_dg_bulk<T, VB, OP_MIN>(b, s);
+    case OP_MAX: return go_dg_bulk<T, VB, OP_MAX>(b, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// 4-, 8- and 16-byte units (its list gathers are cp.async copies); others: cudaErrorNotSupported
+template <typename T>
+cudaError_t launch_dg_bulk_t(int op, int vb, const DgBulkArgs &b, cudaStream_t s) {
+  if constexpr (sizeof(T) >= 4)
+    if (vb == int(sizeof(T))) return dg_bulk_op<T, int(sizeof(T))>(op, b, s);
+  if (vb == 16) return dg_bulk_op<T, 16>(op, b, s);
+  return cudaErrorNotSupported;
+}
+
+template <typename T, int VB>
+static cudaError_t dg_op(int op, const DgLaunch &L) {
+  switch (op) {
+    case OP_SUM: return go_dg<T, VB, OP_SUM>(L);
+    case OP_MIN: return go_dg<T, VB, OP_MIN>(L);
+    case OP_MAX: return go_dg<T, VB, OP_MAX>(L);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_dg_t(int op, int vb, const DgLaunch &L) {
+  if (vb == int(sizeof(T))) return dg_op<T, int(sizeof(T))>(op, L);
+  if (vb == 16) return dg_op<T, 16>(op, L);
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
@@ -119,6 +190,8 @@ cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, v
 #define SFGB_INSTANTIATE(T)                                                                            \
   template cudaError_t launch_rm_t<T>(int, int, int, const RmLaunch &);                                \
   template cudaError_t launch_ts_ops_t<T>(int, int, bool, bool, const TsLaunch &);                     \
+  template cudaError_t launch_dg_t<T>(int, int, const DgLaunch &);                                     \
+  template cudaError_t launch_dg_bulk_t<T>(int, int, const DgBulkArgs &, cudaStream_t);                \
   template cudaError_t launch_maxloc_t<T>(const MaxlocArgs &, int, cudaStream_t);                      \
   template cudaError_t launch_maxloc_scatter_t<T>(const int32_t *, const void *, void *, int64_t, int32_t, \
                                                   cudaStream_t);

@@ -13,7 +13,7 @@
 
 namespace sfgb {
 
-enum { K_BCAST = 1, K_REDUCE = 2, K_FETCH = 3, K_BCAST_MT = 4, K_REDUCE_MT = 5 };
+enum { K_BCAST = 1, K_REDUCE = 2, K_FETCH = 3, K_BCAST_MT = 4, K_REDUCE_MT = 5, K_REDUCE_Z = 6 };
 
 struct Pending {
   int kind;
@@ -48,6 +48,8 @@ struct sf_s {
   int device = -1;
   sfgb::DevBuf blob;                 // all plan arrays
   sfgb::DevPlan dp{};
+  sfgb::DevPlan dp_rest{};           // root-major plan of the roots the diagonal chunks leave out
+  bool has_rest = false;
   std::vector<sfgb::Tile> h_move_tiles;
   const sfgb::Tile *move_tiles = nullptr;
   int32_t n_move_tiles = 0;
@@ -76,11 +78,24 @@ int launched(cudaError_t e);
 TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *src, void *dst, void *upd, int nv,
                int phase);
 RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv);
+RmArgs rm_args_plan(sf_t *sf, const DevPlan &d, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd,
+                    int nv);
+// Whether a deterministic Reduce with `op` and nv vectors per unit runs on the diagonal chunks
+// (then on the root-major plan of the rest).
+inline bool reduce_dg(const sf_t *sf, int32_t op, int nv) {
+  return op != SF_REPLACE && nv == 1 && sf->dp.dg_nchunks > 0;
+}
+DgArgs dg_args(const sf_t *sf, const void *leaf, void *root);
+// Enqueue the deterministic (root-major or diagonal-chunk) Reduce with its fold scratch.
+// With zero_root the roots count as 0 before the operation and are not read.
+int reduce_det_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int vbo,
+                      int nv, void *partial, int32_t *counter, bool zero_root = false);
 int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC after resolving AUTO
 // Whether Reduce with `op` on `dtype` runs on the atomic two-sided kernels: in atomic mode
 // (floating SUM rounds in arrival order there), and in deterministic mode for operations whose
-// result does not depend on the order (integer SUM/MIN/MAX, floating MIN/MAX) while no root has
-// more than kOrderFreeMaxDegree leaves (same-address atomics serialise).
+// result does not depend on the order (integer SUM/MIN/MAX) while no root has more than
+// kOrderFreeMaxDegree leaves (same-address atomics serialise) and the forest has no diagonal
+// chunks.
 constexpr int64_t kOrderFreeMaxDegree = 1024;
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op);
 int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO

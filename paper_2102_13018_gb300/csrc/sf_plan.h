@@ -153,6 +153,36 @@ struct BlockRec {
   int32_t e0;
 };
 
+// Diagonal chunks (deterministic Reduce, see build_diag): chunk c covers root units
+// 32 (c0 + c) .. + 31, one 2-bit code per root -- DG_SKIP (not in this plan), DG_DIAG (its one
+// leaf is the diagonal leaf root + delta), DG_PAIR (the diagonal leaf and one more, whose x
+// entry is its leaf unit, top bit set when it comes after the diagonal one in canonical order),
+// DG_LIST (its x entry points at a list: header -1 - (leaves before | leaves after << 16), a
+// negative number, then the other leaf units in canonical order).  Roots with DG_PAIR or DG_LIST
+// take one x entry each,
+// in root order from xoff on.
+enum : uint32_t { DG_SKIP = 0, DG_DIAG = 1, DG_PAIR = 2, DG_LIST = 3 };
+constexpr int32_t DG_MAX_LEAVES = 64;        // one fold block: D is the plain left fold
+constexpr int32_t DG_MIN_CHUNK_ROOTS = 8;    // a chunk with fewer diagonal roots is left to the rest
+constexpr int64_t DG_MIN_ROOTS = 1024;       // fewer diagonal roots in all: no diagonal plan
+struct DiagChunk {
+  uint32_t lo, hi;   // codes of roots 0..15 and 16..31 of the chunk
+  int32_t xoff;      // first x entry of the chunk
+  int32_t delta;     // diagonal leaf unit - root unit
+};
+static_assert(sizeof(DiagChunk) == 16, "one 16-byte load per chunk");
+// A tile of the staged diagonal-chunk kernel: chunks [c, c + n) of the plan (n <= DG_TILE_CHUNKS),
+// one delta, x entries [xbeg, xend) (at most DG_TILE_XCAP), list entries [lbeg, lend) (at most
+// DG_TILE_LCAP), and whether every root of the tile (below the forest's last root) is in the
+// plan, so the tile may write its roots back whole.
+constexpr int32_t DG_TILE_CHUNKS = 32;
+constexpr int32_t DG_TILE_XCAP = DG_TILE_CHUNKS * 32;   // one x entry per root at most: never binding
+constexpr int32_t DG_TILE_LCAP = 512;
+struct DgTile {
+  int32_t c, n, delta, xbeg, xend, full, lbeg, lend;
+};
+static_assert(sizeof(DgTile) == 32, "tile descriptors are read as two 16-byte vectors");
+
 struct SegCopy {                 // one (root rank -> leaf rank) chunk of the buffer move
   int64_t src0, dst0, n;         // units
 };
@@ -179,6 +209,15 @@ struct DevPlan {
   const RmTile *rm_fetch_tiles;             // masked + pairs + fetch
   int32_t n_rm_fold_tiles, n_rm_fold_nv1_tiles, n_rm_winner_tiles, n_rm_fetch_tiles;
   int32_t n_multi, n_partial_slots, n_counters;
+  // diagonal chunks (deterministic Reduce); the root-major plan of the roots they leave out is a
+  // second DevPlan whose root-major arrays alone are set
+  const DiagChunk *dg_chunks;
+  const int32_t *dg_x, *dg_lists;
+  int32_t dg_c0, dg_nchunks;
+  const int32_t *z_root;   // roots without leaves
+  int32_t n_z_root;
+  const DgTile *dg_tiles;  // tiles of the staged diagonal-chunk kernel
+  int32_t n_dg_tiles;
 };
 
 }  // namespace sfgb

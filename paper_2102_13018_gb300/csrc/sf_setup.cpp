@@ -242,6 +242,304 @@ RmTile rm_tile(int32_t kind, int32_t a, int32_t k0, int32_t cnt) {
   return t;
 }
 
+// Root-major plan (Sec. V.B, extended): single-leaf roots as masked contiguous runs or explicit
+// pairs, multi-leaf roots in CSR form with their leaves in canonical order, cut into fold blocks,
+// and the tile lists of the root-major kernels.  Only edges into roots with deg[r] > 0 take part
+// (deg holds the in-degree of every root, or 0 for a root the plan leaves out).
+void build_rm(int64_t NR, int64_t E, const std::vector<int64_t> &rootu, const std::vector<int64_t> &leafu,
+              const std::vector<int32_t> &deg, HostPlan &plan, int32_t *rm_per_out, int32_t *ch_per_out) {
+  // multi roots: CSR of leaves in canonical order
+  std::vector<int32_t> mid(NR, -1);
+  int32_t M = 0;
+  int64_t multi_edges = 0;
+  for (int64_t r = 0; r < NR; ++r)
+    if (deg[r] >= 2) { mid[r] = M++; multi_edges += deg[r]; }
+  plan.m_root.resize(M);
+  plan.m_ptr.assign(M + 1, 0);
+  for (int64_t r = 0; r < NR; ++r)
+    if (mid[r] >= 0) { plan.m_root[mid[r]] = int32_t(r); plan.m_ptr[mid[r] + 1] = deg[r]; }
+  for (int32_t m = 0; m < M; ++m) plan.m_ptr[m + 1] += plan.m_ptr[m];
+  plan.m_leaf.resize(multi_edges);
+  {
+    std::vector<int32_t> fill(plan.m_ptr.begin(), plan.m_ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t m = mid[rootu[e]];
+      if (m >= 0) plan.m_leaf[fill[m]++] = int32_t(leafu[e]);
+    }
+  }
+  // single-leaf roots
+  std::vector<int64_t> sleaf(NR, -1);
+  for (int64_t e = 0; e < E; ++e)
+    if (deg[rootu[e]] == 1) sleaf[rootu[e]] = leafu[e];
+  {
+    int64_t r0 = -1, l0 = 0, last = -1;
+    std::vector<int64_t> members;
+    auto close = [&]() {
+      if (members.empty()) return;
+      if (int64_t(members.size()) >= kMinMaskedSingles) {
+        MaskedRun mr{};
+        mr.root0 = r0;
+        mr.leaf0 = l0;
+        mr.n = int32_t(last - r0 + 1);
+        mr.mask0 = int64_t(plan.mask.size()) * 32;
+        plan.mask.resize(plan.mask.size() + (mr.n + 31) / 32, 0u);
+        for (int64_t r : members) {
+          const int64_t bit = mr.mask0 + (r - r0);
+          plan.mask[bit >> 5] |= 1u << (bit & 31);
+        }
+        plan.mruns.push_back(mr);
+      } else {
+        for (int64_t r : members) {
+          plan.pr_root.push_back(int32_t(r));
+          plan.pr_leaf.push_back(int32_t(sleaf[r]));
+        }
+      }
+      members.clear();
+    };
+    for (int64_t r = 0; r < NR; ++r) {
+      if (deg[r] != 1) continue;
+      const bool extend = !members.empty() && r - last <= kMaxMaskGap && sleaf[r] - l0 == r - r0 &&
+                          r - r0 < (int64_t(1) << 30);
+      if (!extend) {
+        close();
+        r0 = r;
+        l0 = sleaf[r];
+      }
+      members.push_back(r);
+      last = r;
+    }
+    close();
+  }
+  // fold blocks of multi roots
+  std::vector<int32_t> blk_m;   // block -> multi root (host only, for tiling)
+  std::vector<uint8_t> heavy(M, 0);
+  for (int32_t m = 0; m < M; ++m) {
+    const int32_t d = plan.m_ptr[m + 1] - plan.m_ptr[m];
+    const int32_t nch = (d + FOLD_BLOCK - 1) / FOLD_BLOCK;
+    int32_t comb = -1;
+    if (nch > 1) {
+      comb = int32_t(plan.combs.size());
+      const int32_t nsuper = (nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
+      plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_partial_slots + nch, plan.n_counters, nch,
+                                plan.m_ptr[m], plan.m_root[m]});
+      plan.n_partial_slots += nch + nsuper;
+      plan.n_counters += nsuper + 1;
+    }
+    for (int32_t c = 0; c < nch; ++c) {
+      const int32_t e0 = plan.m_ptr[m] + c * FOLD_BLOCK;
+      plan.blocks.push_back(Block{plan.m_root[m], e0, std::min(FOLD_BLOCK, plan.m_ptr[m + 1] - e0), comb});
+      plan.block_recs.push_back(BlockRec{comb < 0 ? plan.m_root[m] : -(comb + 1), e0});
+      blk_m.push_back(m);
+    }
+    heavy[m] = nch >= 16;
+  }
+  plan.block_recs.push_back(BlockRec{0, int32_t(plan.m_leaf.size())});   // sentinel
+  // tiles, ordered by the first root they touch (heavy multi roots first)
+  struct Keyed { int64_t key; RmTile t; };
+  std::vector<Keyed> common;
+  int64_t single_work = int64_t(plan.pr_root.size());
+  for (const MaskedRun &mr : plan.mruns) single_work += mr.n;
+  const int32_t rm_per = tile_size(single_work, RM_TILE_EDGES_MIN, RM_TILE_EDGES);   // a multiple of 32
+  const int32_t ch_per = tile_size(int64_t(plan.blocks.size()), RM_TILE_CHUNKS_MIN, RM_TILE_CHUNKS);
+  if (rm_per_out) *rm_per_out = rm_per;
+  if (ch_per_out) *ch_per_out = ch_per;
+  for (size_t i = 0; i < plan.mruns.size(); ++i)
+    for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += rm_per) {
+      RmTile t = rm_tile(T_MASKED, int32_t(i), int32_t(k0),
+                         int32_t(std::min<int64_t>(rm_per, plan.mruns[i].n - k0)));
+      t.root0 = plan.mruns[i].root0;
+      t.leaf0 = plan.mruns[i].leaf0;
+      t.mask0 = plan.mruns[i].mask0;
+      common.push_back({plan.mruns[i].root0 + k0, t});
+    }
+  for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += rm_per)
+    common.push_back({plan.pr_root[i], rm_tile(T_PAIRS, int32_t(i), 0,
+                                               int32_t(std::min<int64_t>(rm_per, plan.pr_root.size() - i)))});
+  const int64_t heavy_key = -(int64_t(1) << 40);
+  auto finish = [&](std::vector<Keyed> extra, std::vector<RmTile> &out) {
+    extra.insert(extra.end(), common.begin(), common.end());
+    std::stable_sort(extra.begin(), extra.end(), [](const Keyed &a, const Keyed &b) { return a.key < b.key; });
+    out.clear();
+    for (auto &k : extra) out.push_back(k.t);
+  };
+  // chunk tiles: at most ch_per blocks and ch_edges leaf entries per tile (the shared-memory
+  // stage of the kernel that reads them); one list for the general Reduce kernel, one cut at
+  // half the leaves for the one-vector-unit kernel
+  auto chunk_tiles = [&](int64_t max_edges, std::vector<RmTile> &out) {
+    const int64_t ch_edges = max_edges * ch_per / RM_TILE_CHUNKS;
+    std::vector<Keyed> ch;
+    const int64_t nblocks = int64_t(plan.blocks.size());
+    int64_t c = 0;
+    while (c < nblocks) {
+      const int32_t m = blk_m[c];
+      int64_t c1 = c, edges = 0;
+      if (heavy[m]) {   // a heavy root's blocks get tiles of their own, scheduled first
+        while (c1 < nblocks && blk_m[c1] == m && c1 - c < ch_per / 4 && edges + plan.blocks[c1].n <= ch_edges)
+          edges += plan.blocks[c1++].n;
+      } else {
+        while (c1 < nblocks && !heavy[blk_m[c1]] && c1 - c < ch_per && edges + plan.blocks[c1].n <= ch_edges)
+          edges += plan.blocks[c1++].n;
+      }
+      RmTile t = rm_tile(T_CHUNKS, int32_t(c), plan.blocks[c].e0, int32_t(c1 - c));
+      t.e1 = int64_t(plan.blocks[c].e0) + edges;
+      ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]), t});
+      c = c1;
+    }
+    finish(ch, out);
+  };
+  chunk_tiles(RM_TILE_CHUNK_EDGES, plan.rm_fold_tiles);
+  chunk_tiles(RM_TILE_CHUNK_EDGES_NV1, plan.rm_fold_nv1_tiles);
+  {
+    std::vector<Keyed> w;
+    for (int32_t m = 0; m < M; m += RM_TILE_ROOTS)
+      w.push_back({plan.m_root[m], rm_tile(T_WINNERS, m, 0, std::min<int32_t>(RM_TILE_ROOTS, M - m))});
+    finish(w, plan.rm_winner_tiles);
+  }
+  {
+    std::vector<Keyed> f;
+    int32_t m = 0;
+    while (m < M) {
+      int32_t m1 = m;
+      int64_t edges = 0;
+      while (m1 < M && m1 - m < RM_TILE_FETCH && (edges < 4096 || m1 == m)) {
+        edges += plan.m_ptr[m1 + 1] - plan.m_ptr[m1];
+        ++m1;
+      }
+      f.push_back({plan.m_root[m], rm_tile(T_FETCH, m, 0, m1 - m)});
+      m = m1;
+    }
+    finish(f, plan.rm_fetch_tiles);
+  }
+}
+
+// Diagonal chunks: a root-streaming plan for the deterministic Reduce of forests in which most
+// roots own one leaf at a fixed offset from themselves (leaf unit = root unit + delta) -- the
+// owned entries of a rank's local vector in the SpMV scatter of Sec. IV.A, whose ghost columns
+// are the other leaves.  Roots are taken 32 at a time (one warp), in root order, so the roots
+// and their diagonal leaves stream through fully used sectors; a root's other leaves (at most
+// DG_MAX_LEAVES - 1) are listed in canonical order, and the diagonal leaf keeps its canonical
+// place in the fold.  Roots that do not fit are left to the root-major plan of the rest.
+// Returns false (and builds nothing) when too few roots fit for the plan to pay.
+bool build_diag(int64_t NR, int64_t E, const std::vector<int64_t> &rootu, const std::vector<int64_t> &leafu,
+                const std::vector<int32_t> &deg, DiagHost &dg, std::vector<uint8_t> &covered) {
+  dg = DiagHost();
+  if (NR == 0 || E == 0) return false;
+  // CSR of every root's leaves, canonical order inside a root (stable counting sort)
+  std::vector<int32_t> ptr(NR + 1, 0), eleaf(E);
+  for (int64_t r = 0; r < NR; ++r) ptr[r + 1] = ptr[r] + deg[r];
+  {
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) eleaf[fill[rootu[e]]++] = int32_t(leafu[e]);
+  }
+  // per chunk of 32 roots: the offset most of its roots' leaves share, and how many roots have it
+  const int64_t NC = (NR + 31) / 32;
+  std::vector<int32_t> cdelta(NC, 0), cgood(NC, 0);
+  std::vector<int64_t> cand;
+  int64_t good = 0, connected = 0;
+  for (int64_t c = 0; c < NC; ++c) {
+    cand.clear();
+    for (int64_t u = c * 32; u < std::min(NR, c * 32 + 32); ++u) {
+      connected += deg[u] > 0;
+      if (deg[u] < 1 || deg[u] > DG_MAX_LEAVES) continue;
+      for (int32_t k = ptr[u]; k < ptr[u + 1]; ++k) cand.push_back(int64_t(eleaf[k]) - u);
+    }
+    if (cand.empty()) continue;
+    std::sort(cand.begin(), cand.end());   // a root's leaves differ, so a value counts roots
+    int64_t best = cand[0], best_n = 0;
+    for (size_t i = 0; i < cand.size();) {
+      size_t j = i;
+      while (j < cand.size() && cand[j] == cand[i]) ++j;
+      if (int64_t(j - i) > best_n) { best_n = int64_t(j - i); best = cand[i]; }
+      i = j;
+    }
+    if (best_n >= DG_MIN_CHUNK_ROOTS) {
+      cdelta[c] = int32_t(best);
+      cgood[c] = int32_t(best_n);
+      good += best_n;
+    }
+  }
+  if (good < DG_MIN_ROOTS || 2 * good < connected) return false;
+  int64_t c_lo = 0, c_hi = NC;
+  while (!cgood[c_lo]) ++c_lo;
+  while (!cgood[c_hi - 1]) --c_hi;
+  covered.assign(NR, 0);
+  dg.c0 = c_lo;
+  dg.chunks.reserve(c_hi - c_lo);
+  for (int64_t c = c_lo; c < c_hi; ++c) {
+    DiagChunk rec{0u, 0u, int32_t(dg.x.size()), cdelta[c]};
+    if (cgood[c]) {
+      for (int32_t lane = 0; lane < 32; ++lane) {
+        const int64_t u = c * 32 + lane;
+        if (u >= NR) break;
+        const int32_t n = deg[u];
+        if (n < 1 || n > DG_MAX_LEAVES) continue;
+        int32_t k = -1;
+        for (int32_t i = 0; i < n; ++i)
+          if (int64_t(eleaf[ptr[u] + i]) - u == cdelta[c]) { k = i; break; }
+        if (k < 0) continue;
+        uint32_t code;
+        if (n == 1) {
+          code = DG_DIAG;
+        } else if (n == 2) {
+          // the other leaf, with the top bit set when it comes after the diagonal leaf
+          const int32_t other = eleaf[ptr[u] + 1 - k];
+          dg.x.push_back(k == 0 ? int32_t(uint32_t(other) | 0x80000000u) : other);
+          code = DG_PAIR;
+        } else {
+          dg.x.push_back(int32_t(dg.lists.size()));
+          dg.lists.push_back(-1 - (k | ((n - 1 - k) << 16)));   // leaves before | after the diagonal one
+          for (int32_t i = 0; i < n; ++i)
+            if (i != k) dg.lists.push_back(eleaf[ptr[u] + i]);
+          code = DG_LIST;
+          ++dg.list_roots;
+        }
+        (lane < 16 ? rec.lo : rec.hi) |= code << (2 * (lane & 15));
+        covered[u] = 1;
+        ++dg.roots;
+        dg.extras += n - 1;
+      }
+    }
+    dg.chunks.push_back(rec);
+  }
+  // tiles: runs of chunks with one delta, at most DG_TILE_CHUNKS chunks, DG_TILE_XCAP x entries
+  // and DG_TILE_LCAP list entries each; chunks without any covered root are left out.  A
+  // chunk's list entries start at the list of its first DG_LIST root (lists are in root order).
+  const int64_t nch = int64_t(dg.chunks.size());
+  auto x_end = [&](int64_t k) { return k + 1 < nch ? dg.chunks[k + 1].xoff : int32_t(dg.x.size()); };
+  std::vector<int32_t> lfirst(nch + 1, int32_t(dg.lists.size()));   // first list entry of chunk k
+  for (int64_t k = nch - 1; k >= 0; --k) {
+    lfirst[k] = lfirst[k + 1];
+    const DiagChunk &ch = dg.chunks[k];
+    for (int32_t lane = 31, xi = x_end(k) - 1; lane >= 0; --lane) {
+      const uint32_t code = ((lane < 16 ? ch.lo : ch.hi) >> (2 * (lane & 15))) & 3u;
+      if (code == DG_LIST) lfirst[k] = dg.x[xi];
+      if (code >= DG_PAIR) --xi;
+    }
+  }
+  for (int64_t k = 0; k < nch;) {
+    if (!dg.chunks[k].lo && !dg.chunks[k].hi) { ++k; continue; }
+    int64_t k1 = k + 1;
+    while (k1 < nch && k1 - k < DG_TILE_CHUNKS && (dg.chunks[k1].lo || dg.chunks[k1].hi) &&
+           dg.chunks[k1].delta == dg.chunks[k].delta && x_end(k1) - dg.chunks[k].xoff <= DG_TILE_XCAP &&
+           lfirst[k1 + 1] - lfirst[k] <= DG_TILE_LCAP)
+      ++k1;
+    DgTile t{};
+    t.c = int32_t(k);
+    t.n = int32_t(k1 - k);
+    t.delta = dg.chunks[k].delta;
+    t.xbeg = dg.chunks[k].xoff;
+    t.xend = x_end(k1 - 1);
+    t.lbeg = lfirst[k];
+    t.lend = lfirst[k1];
+    t.full = 1;
+    for (int64_t u = (c_lo + k) * 32; u < std::min(NR, (c_lo + k1) * 32); ++u)
+      if (!covered[u]) { t.full = 0; break; }
+    dg.tiles.push_back(t);
+    k = k1;
+  }
+  return true;
+}
+
 }  // namespace
 
 int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
@@ -337,168 +635,24 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       }
     }
 
-    // ---- root-major plan
-    // multi roots: CSR of leaves in canonical order
-    std::vector<int32_t> mid(NR, -1);
-    int32_t M = 0;
-    int64_t multi_edges = 0;
     for (int64_t r = 0; r < NR; ++r)
-      if (deg[r] >= 2) { mid[r] = M++; multi_edges += deg[r]; }
-    plan.m_root.resize(M);
-    plan.m_ptr.assign(M + 1, 0);
-    for (int64_t r = 0; r < NR; ++r)
-      if (mid[r] >= 0) { plan.m_root[mid[r]] = int32_t(r); plan.m_ptr[mid[r] + 1] = deg[r]; }
-    for (int32_t m = 0; m < M; ++m) plan.m_ptr[m + 1] += plan.m_ptr[m];
-    plan.m_leaf.resize(multi_edges);
-    {
-      std::vector<int32_t> fill(plan.m_ptr.begin(), plan.m_ptr.end() - 1);
-      for (int64_t e = 0; e < E; ++e) {
-        const int32_t m = mid[rootu[e]];
-        if (m >= 0) plan.m_leaf[fill[m]++] = int32_t(leafu[e]);
-      }
-    }
-    // single-leaf roots
-    std::vector<int64_t> sleaf(NR, -1);
-    for (int64_t e = 0; e < E; ++e)
-      if (deg[rootu[e]] == 1) sleaf[rootu[e]] = leafu[e];
-    {
-      int64_t r0 = -1, l0 = 0, last = -1;
-      std::vector<int64_t> members;
-      auto close = [&]() {
-        if (members.empty()) return;
-        if (int64_t(members.size()) >= kMinMaskedSingles) {
-          MaskedRun mr{};
-          mr.root0 = r0;
-          mr.leaf0 = l0;
-          mr.n = int32_t(last - r0 + 1);
-          mr.mask0 = int64_t(plan.mask.size()) * 32;
-          plan.mask.resize(plan.mask.size() + (mr.n + 31) / 32, 0u);
-          for (int64_t r : members) {
-            const int64_t bit = mr.mask0 + (r - r0);
-            plan.mask[bit >> 5] |= 1u << (bit & 31);
-          }
-          plan.mruns.push_back(mr);
-        } else {
-          for (int64_t r : members) {
-            plan.pr_root.push_back(int32_t(r));
-            plan.pr_leaf.push_back(int32_t(sleaf[r]));
-          }
-        }
-        members.clear();
-      };
-      for (int64_t r = 0; r < NR; ++r) {
-        if (deg[r] != 1) continue;
-        const bool extend = !members.empty() && r - last <= kMaxMaskGap && sleaf[r] - l0 == r - r0 &&
-                            r - r0 < (int64_t(1) << 30);
-        if (!extend) {
-          close();
-          r0 = r;
-          l0 = sleaf[r];
-        }
-        members.push_back(r);
-        last = r;
-      }
-      close();
-    }
-    // fold blocks of multi roots
-    std::vector<int32_t> blk_m;   // block -> multi root (host only, for tiling)
-    std::vector<uint8_t> heavy(M, 0);
-    for (int32_t m = 0; m < M; ++m) {
-      const int32_t d = plan.m_ptr[m + 1] - plan.m_ptr[m];
-      const int32_t nch = (d + FOLD_BLOCK - 1) / FOLD_BLOCK;
-      int32_t comb = -1;
-      if (nch > 1) {
-        comb = int32_t(plan.combs.size());
-        const int32_t nsuper = (nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
-        plan.combs.push_back(Comb{plan.n_partial_slots, plan.n_partial_slots + nch, plan.n_counters, nch,
-                                  plan.m_ptr[m], plan.m_root[m]});
-        plan.n_partial_slots += nch + nsuper;
-        plan.n_counters += nsuper + 1;
-      }
-      for (int32_t c = 0; c < nch; ++c) {
-        const int32_t e0 = plan.m_ptr[m] + c * FOLD_BLOCK;
-        plan.blocks.push_back(Block{plan.m_root[m], e0, std::min(FOLD_BLOCK, plan.m_ptr[m + 1] - e0), comb});
-        plan.block_recs.push_back(BlockRec{comb < 0 ? plan.m_root[m] : -(comb + 1), e0});
-        blk_m.push_back(m);
-      }
-      heavy[m] = nch >= 16;
-    }
-    plan.block_recs.push_back(BlockRec{0, int32_t(plan.m_leaf.size())});   // sentinel
-    // tiles, ordered by the first root they touch (heavy multi roots first)
-    struct Keyed { int64_t key; RmTile t; };
-    std::vector<Keyed> common;
-    int64_t single_work = int64_t(plan.pr_root.size());
-    for (const MaskedRun &mr : plan.mruns) single_work += mr.n;
-    const int32_t rm_per = tile_size(single_work, RM_TILE_EDGES_MIN, RM_TILE_EDGES);   // a multiple of 32
-    const int32_t ch_per = tile_size(int64_t(plan.blocks.size()), RM_TILE_CHUNKS_MIN, RM_TILE_CHUNKS);
+      if (deg[r] == 0) plan.z_root.push_back(int32_t(r));
+
+    // ---- root-major plan over every root, then the diagonal chunks and the root-major plan of the
+    // roots they leave out
+    int32_t rm_per = 0, ch_per = 0;
+    build_rm(NR, E, rootu, leafu, deg, plan, &rm_per, &ch_per);
     info.rm_tile_edges = rm_per;
     info.rm_tile_blocks = ch_per;
-    for (size_t i = 0; i < plan.mruns.size(); ++i)
-      for (int64_t k0 = 0; k0 < plan.mruns[i].n; k0 += rm_per) {
-        RmTile t = rm_tile(T_MASKED, int32_t(i), int32_t(k0),
-                           int32_t(std::min<int64_t>(rm_per, plan.mruns[i].n - k0)));
-        t.root0 = plan.mruns[i].root0;
-        t.leaf0 = plan.mruns[i].leaf0;
-        t.mask0 = plan.mruns[i].mask0;
-        common.push_back({plan.mruns[i].root0 + k0, t});
-      }
-    for (int64_t i = 0; i < int64_t(plan.pr_root.size()); i += rm_per)
-      common.push_back({plan.pr_root[i], rm_tile(T_PAIRS, int32_t(i), 0,
-                                                 int32_t(std::min<int64_t>(rm_per, plan.pr_root.size() - i)))});
-    const int64_t heavy_key = -(int64_t(1) << 40);
-    auto finish = [&](std::vector<Keyed> extra, std::vector<RmTile> &out) {
-      extra.insert(extra.end(), common.begin(), common.end());
-      std::stable_sort(extra.begin(), extra.end(), [](const Keyed &a, const Keyed &b) { return a.key < b.key; });
-      out.clear();
-      for (auto &k : extra) out.push_back(k.t);
-    };
-    // chunk tiles: at most ch_per blocks and ch_edges leaf entries per tile (the shared-memory
-    // stage of the kernel that reads them); one list for the general Reduce kernel, one cut at
-    // half the leaves for the one-vector-unit kernel
-    auto chunk_tiles = [&](int64_t max_edges, std::vector<RmTile> &out) {
-      const int64_t ch_edges = max_edges * ch_per / RM_TILE_CHUNKS;
-      std::vector<Keyed> ch;
-      const int64_t nblocks = int64_t(plan.blocks.size());
-      int64_t c = 0;
-      while (c < nblocks) {
-        const int32_t m = blk_m[c];
-        int64_t c1 = c, edges = 0;
-        if (heavy[m]) {   // a heavy root's blocks get tiles of their own, scheduled first
-          while (c1 < nblocks && blk_m[c1] == m && c1 - c < ch_per / 4 && edges + plan.blocks[c1].n <= ch_edges)
-            edges += plan.blocks[c1++].n;
-        } else {
-          while (c1 < nblocks && !heavy[blk_m[c1]] && c1 - c < ch_per && edges + plan.blocks[c1].n <= ch_edges)
-            edges += plan.blocks[c1++].n;
-        }
-        RmTile t = rm_tile(T_CHUNKS, int32_t(c), plan.blocks[c].e0, int32_t(c1 - c));
-        t.e1 = int64_t(plan.blocks[c].e0) + edges;
-        ch.push_back({heavy[m] ? heavy_key + plan.m_root[m] : int64_t(plan.m_root[m]), t});
-        c = c1;
-      }
-      finish(ch, out);
-    };
-    chunk_tiles(RM_TILE_CHUNK_EDGES, plan.rm_fold_tiles);
-    chunk_tiles(RM_TILE_CHUNK_EDGES_NV1, plan.rm_fold_nv1_tiles);
     {
-      std::vector<Keyed> w;
-      for (int32_t m = 0; m < M; m += RM_TILE_ROOTS)
-        w.push_back({plan.m_root[m], rm_tile(T_WINNERS, m, 0, std::min<int32_t>(RM_TILE_ROOTS, M - m))});
-      finish(w, plan.rm_winner_tiles);
-    }
-    {
-      std::vector<Keyed> f;
-      int32_t m = 0;
-      while (m < M) {
-        int32_t m1 = m;
-        int64_t edges = 0;
-        while (m1 < M && m1 - m < RM_TILE_FETCH && (edges < 4096 || m1 == m)) {
-          edges += plan.m_ptr[m1 + 1] - plan.m_ptr[m1];
-          ++m1;
-        }
-        f.push_back({plan.m_root[m], rm_tile(T_FETCH, m, 0, m1 - m)});
-        m = m1;
+      std::vector<uint8_t> covered;
+      if (build_diag(NR, E, rootu, leafu, deg, plan.dg, covered)) {
+        std::vector<int32_t> rest_deg(deg);
+        for (int64_t r = 0; r < NR; ++r)
+          if (covered[r]) rest_deg[r] = 0;
+        plan.rest = std::make_shared<HostPlan>();
+        build_rm(NR, E, rootu, leafu, rest_deg, *plan.rest, nullptr, nullptr);
       }
-      finish(f, plan.rm_fetch_tiles);
     }
 
     // ---- statistics
@@ -511,8 +665,13 @@ int analyze(const Graph &g, HostPlan &plan, sf_info &info) {
       info.connected_roots += deg[r] > 0;
     }
     info.has_dup_roots = info.max_in_degree > 1;
-    info.multi_roots = M;
-    info.multi_edges = multi_edges;
+    info.multi_roots = int64_t(plan.m_root.size());
+    info.multi_edges = int64_t(plan.m_leaf.size());
+    info.dg_chunks = int64_t(plan.dg.chunks.size());
+    info.dg_roots = plan.dg.roots;
+    info.dg_extra_leaves = plan.dg.extras;
+    info.dg_list_roots = plan.dg.list_roots;
+    info.dg_rest_roots = plan.rest ? info.connected_roots - plan.dg.roots : 0;
     info.rm_masked_runs = int64_t(plan.mruns.size());
     for (auto &mr : plan.mruns)
       for (int32_t k = 0; k < mr.n; ++k)

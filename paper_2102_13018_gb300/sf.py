@@ -281,6 +281,28 @@ class StarForest:
         check(self._lib.sf_reduce_end(*args), "sf_reduce_end")
         return rootdata
 
+    def reduce_from_zero(self, leafdata, rootdata, op: str = "SUM", bs: Optional[int] = None, stream=None):
+        """rootdata = Reduce(op) of leafdata into roots that start at zero (every root written,
+        roots without leaves get 0; the old rootdata is never read)."""
+        args = (self._h, self._unit(rootdata, self.nroots_total, bs), self._ptr(leafdata), self._ptr(rootdata),
+                OPS[op], self._stream(stream))
+        check(self._lib.sf_reduce_from_zero_begin(*args), "sf_reduce_from_zero_begin")
+        check(self._lib.sf_reduce_from_zero_end(*args), "sf_reduce_from_zero_end")
+        return rootdata
+
+    def zero_leafless_roots(self, rootdata, argleaf=None, bs: Optional[int] = None, stream=None):
+        """Roots without leaves -> 0 (and their argleaf entries -> -1); other roots untouched."""
+        u = self._unit(rootdata, self.nroots_total, bs)
+        check(self._lib.sf_zero_leafless_roots(self._h, u, self._ptr(rootdata), self._ptr(argleaf),
+                                               self._stream(stream)), "sf_zero_leafless_roots")
+        return rootdata
+
+    def all_leaves_connected(self) -> bool:
+        """Whether every leaf unit of the layout has a root (a Bcast REPLACE then writes all)."""
+        if getattr(self, "_all_connected", None) is None:
+            self._all_connected = self.info()["nedges"] == self.leaf_extent
+        return self._all_connected
+
     def fetch_and_op_begin(self, rootdata, leafdata, leafupdate, op: str = "SUM", bs=None, stream=None):
         u = self._unit(rootdata, self.nroots_total, bs)
         check(self._lib.sf_fetch_and_op_begin(self._h, u, self._ptr(rootdata), self._ptr(leafdata),

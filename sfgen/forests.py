@@ -200,6 +200,39 @@ def cfg2_halo(n: int = 256, m: int = 4, include_owned: bool = False) -> Forest:
 # Workload family 4: batched, Zipf in-degree
 # --------------------------------------------------------------------------------------
 
+def owned_plus_ghosts(seed: int, nroots=(1000, 2048, 37, 3001, 700, 96), keep: float = 0.9,
+                      ghosts_per_rank: int = 900, heavy: int = 3, shuffled_rank: int = 2) -> Forest:
+    """The shape of the SpMV scatter (Sec. IV.A) with its corner cases: every rank q lists
+    its owned entries first -- leaf i -> root (q, i), each kept with probability `keep` --
+    then ghost leaves pointing at random roots of any rank (in random order, so a root's
+    ghosts fall before or after its owned leaf in canonical order), 70 or 30 of them piled on
+    each of `heavy` roots per rank so that some roots get more than 64 leaves.  On rank
+    `shuffled_rank` the owned leaves are permuted, so they sit at no fixed offset from their
+    roots.  Rank sizes that are not multiples of 32 leave chunks of 32 roots straddling two
+    ranks.  ilocal is given (owned leaves keep local index i, ghosts follow at n_q + k)."""
+    P = len(nroots)
+    nroots = np.array(nroots, dtype=np.int64)
+    total = int(nroots.sum())
+    rootoff = np.concatenate([[0], np.cumsum(nroots)])
+    il, rr, ri, nl = [], [], [], []
+    for q in range(P):
+        n = int(nroots[q])
+        own = np.nonzero(rng.uniform01(seed, 10 + q, n) < keep)[0]
+        own_root = own.copy()
+        if q == shuffled_rank:
+            own_root = own[np.argsort(rng.u64(seed, 20 + q, own.size), kind="stable")]
+        g = rng.randint(seed, 30 + q, ghosts_per_rank, 0, total)
+        hot = rng.randint(seed, 40 + q, heavy, 0, total)
+        g = np.concatenate([g, np.repeat(hot, [70] + [30] * (heavy - 1))])
+        g = g[np.argsort(rng.u64(seed, 50 + q, g.size), kind="stable")]
+        gr = np.searchsorted(rootoff, g, side="right") - 1
+        il.append(np.concatenate([own, n + np.arange(g.size)]).astype(np.int64))
+        rr.append(np.concatenate([np.full(own.size, q), gr]).astype(np.int32))
+        ri.append(np.concatenate([own_root, g - rootoff[gr]]).astype(np.int64))
+        nl.append(own.size + g.size)
+    return Forest(P, nroots, np.array(nl), il, rr, ri, name=f"owned_plus_ghosts{seed}")
+
+
 def zipf_forest(seed: int, tag: int, nleaves: int, nroots: int, nranks: int,
                 s: float = 1.1) -> Forest:
     """nleaves leaves split evenly over nranks (ilocal None); roots split evenly; each

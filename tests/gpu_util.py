@@ -56,3 +56,29 @@ def assert_atomic_sum_close(got, want, f, dtype, bs, leaf, root0, what):
         i = bad[0]
         raise AssertionError(f"{what}: {bad.size} outside bound; first at {i}: err {err[i]} bound {bound[i]}")
     return float(np.max(err / np.maximum(absum, 1e-300))) if err.size else 0.0
+
+
+def signed_zero_forest(nroots=4000, seed=93):
+    """Roots of in-degree 1..9 on three ranks, leaves in random rank order: the data below
+    gives every root a mix of +0 and -0 leaves, so MIN/MAX ties are decided by canonical order."""
+    deg = (np.arange(nroots) % 9) + 1
+    owner = np.repeat(np.arange(nroots), deg)
+    owner = owner[np.argsort(sfgen.rng.u64(seed, 1, owner.size), kind="stable")]
+    per = -(-nroots // 3)
+    cuts = np.linspace(0, owner.size, 4).astype(int)
+    rr = [(owner[cuts[q]:cuts[q + 1]] // per).astype(np.int32) for q in range(3)]
+    ri = [(owner[cuts[q]:cuts[q + 1]] % per).astype(np.int64) for q in range(3)]
+    roots = np.array([min(per, nroots - p * per) for p in range(3)])
+    return sfgen.Forest(3, roots, np.diff(cuts), [None] * 3, rr, ri, name="signed_zero")
+
+
+def signed_zero_data(f, dtype, bs, seed):
+    """Leaves +0 or -0 at random; roots -1, +0 or -0 (MAX) / +1, +0 or -0 (MIN)."""
+    ro, lo = oracle.layout(f)
+    npt = {"fp32": np.float32, "fp64": np.float64}[dtype]
+    sgn = sfgen.rng.u64(seed, 1, int(lo[-1]) * bs) & np.uint64(1)
+    leaf = np.where(sgn == 1, npt(-0.0), npt(0.0)).astype(npt)
+    pick = sfgen.rng.u64(seed, 2, int(ro[-1]) * bs) % np.uint64(3)
+    root = np.choose(pick.astype(np.int64), [npt(-1.0), npt(0.0), npt(-0.0)]).astype(npt)
+    return root, leaf
+

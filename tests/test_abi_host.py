@@ -234,3 +234,54 @@ def test_compose_checks_layouts_and_degrees():
     info = ab.analyze().info()
     assert info["nedges"] == 10                       # rank 1's isolated leaf 2 drops out
     assert ab.rootoff.tolist() == a.rootoff.tolist()
+
+
+def _diagonal_chunks_numpy(f, block=64, min_chunk=8, min_roots=1024):
+    """The diagonal-chunk rule restated with numpy: in each chunk of 32 root units, among
+    roots of in-degree 1..block, the offset leaf - root shared by the most roots (the smallest
+    such offset on a tie) is the chunk's, if at least min_chunk roots share it; those roots
+    are covered.  The plan exists when at least min_roots roots, and half of the connected
+    roots, are covered.  Returns (covered mask, in-degrees, number of chunks) or None."""
+    L, R = npref.edge_arrays(f)
+    NR = int(np.sum(f.nroots))
+    deg = np.bincount(R, minlength=NR)
+    ok = (deg[R] >= 1) & (deg[R] <= block)
+    d, r = (L - R)[ok], R[ok]
+    covered = np.zeros(NR, bool)
+    good_chunks = []
+    for c in np.unique(r // 32):
+        sel = (r // 32) == c
+        vals, counts = np.unique(d[sel], return_counts=True)
+        best = int(np.argmax(counts))           # first maximum: the smallest offset
+        if counts[best] >= min_chunk:
+            covered[r[sel][d[sel] == vals[best]]] = True
+            good_chunks.append(c)
+    if covered.sum() < min_roots or 2 * covered.sum() < (deg > 0).sum():
+        return None
+    return covered, deg, good_chunks[-1] - good_chunks[0] + 1
+
+
+@pytest.mark.parametrize("f", [sfgen.owned_plus_ghosts(5), sfgen.owned_plus_ghosts(6, keep=0.6),
+                               sfgen.cfg3_spmv(1 << 15, 4), sfgen.zipf_forest(8, 1, 20000, 3000, 4),
+                               sfgen.cfg1_plain_tiny()], ids=lambda f: f.name)
+def test_diagonal_chunk_plan_statistics(f):
+    info = StarForest.from_forest(f).analyze().info()
+    want = _diagonal_chunks_numpy(f)
+    if want is None:
+        assert info["dg_chunks"] == 0 and info["dg_roots"] == 0 and info["dg_rest_roots"] == 0
+        return
+    covered, deg, nchunks = want
+    assert info["dg_chunks"] == nchunks
+    assert info["dg_roots"] == int(covered.sum())
+    assert info["dg_extra_leaves"] == int((deg[covered] - 1).sum())
+    assert info["dg_list_roots"] == int((deg[covered] >= 3).sum())
+    assert info["dg_rest_roots"] == int(((deg > 0) & ~covered).sum())
+
+
+def test_diagonal_chunks_cover_the_spmv_scatter_and_leave_corner_cases_to_the_rest():
+    spmv = StarForest.from_forest(sfgen.cfg3_spmv(1 << 15, 4)).analyze().info()
+    assert spmv["dg_roots"] == spmv["connected_roots"] and spmv["dg_rest_roots"] == 0
+    mix = StarForest.from_forest(sfgen.owned_plus_ghosts(5)).analyze().info()
+    # roots without an owned leaf, roots of the shuffled rank and roots of more than 64 leaves
+    assert mix["dg_rest_roots"] > 0 and mix["dg_list_roots"] > 0
+    assert 0 < mix["dg_roots"] < mix["connected_roots"]

@@ -65,6 +65,63 @@ def test_gradcheck_fp64_slice():
     assert torch.autograd.gradcheck(lambda t: sfa.reduce(sf, t, "MAX"), (y,), eps=1e-6, atol=1e-7)
 
 
+@pytest.fixture(scope="module")
+def powerlaw_root_slice():
+    """The full power-law message-passing forest (2^20 roots, 2^23 leaves) cut to its roots
+    below 1024 by sf_create_embedded_root_sf (Sec. III.C: the edges of the selected roots, with
+    nothing renumbered, so the slice keeps the full buffer layout).  Returns the slice, the
+    leaf and root units of its edges in canonical order, and the layout sizes."""
+    f = sfgen.cfg5_powerlaw()
+    full = StarForest.from_forest(f)
+    sl = full.embedded_roots(np.arange(1024)).setup().set_mode("deterministic")
+    L, R = npref.edge_arrays(f)
+    keep = R < 1024
+    assert sl.info()["nedges"] == int(keep.sum()) > 1024
+    return sl, L[keep], R[keep]
+
+
+def test_gradcheck_fp64_on_embedded_root_slice(powerlaw_root_slice):
+    """fp64 gradcheck of Bcast, Reduce SUM and Reduce MAX on the 2^10-root slice of the full
+    power-law forest.  The checked function maps the 1024 selected roots' values (or the slice's
+    leaf values) through the full-layout operation and back out, so the Jacobian stays small."""
+    sl, L, R = powerlaw_root_slice
+    bs = 2
+    Lt, sel = torch.from_numpy(L).cuda(), torch.arange(1024, device="cuda")
+
+    def bcast_slice(xs):
+        x = torch.zeros(sl.nroots_total, bs, dtype=xs.dtype, device="cuda").index_copy(0, sel, xs)
+        return sfa.bcast(sl, x).index_select(0, Lt)
+
+    def reduce_slice(ys, op):
+        y = torch.zeros(sl.leaf_extent, bs, dtype=ys.dtype, device="cuda").index_copy(0, Lt, ys)
+        return sfa.reduce(sl, y, op).index_select(0, sel)
+
+    xs = torch.rand(1024, bs, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(bcast_slice, (xs,), eps=1e-6, atol=1e-7, fast_mode=True)
+    ys = torch.rand(len(L), bs, dtype=torch.float64, device="cuda", requires_grad=True)   # no ties
+    assert torch.autograd.gradcheck(lambda t: reduce_slice(t, "SUM"), (ys,), eps=1e-6, atol=1e-7, fast_mode=True)
+    assert torch.autograd.gradcheck(lambda t: reduce_slice(t, "MAX"), (ys,), eps=1e-6, atol=1e-7, fast_mode=True)
+
+
+def test_embedded_root_slice_gradients_are_dense_transposes(powerlaw_root_slice):
+    """On the slice, Bcast is lvec[L_e] = x[R_e] and its gradient the sum of g[L_e] into R_e;
+    integer-valued fp64 data makes every sum exact.  Leaves of other roots stay 0."""
+    sl, L, R = powerlaw_root_slice
+    bs = 3
+    x = torch.randint(-9, 9, (sl.nroots_total, bs), device="cuda").double().requires_grad_(True)
+    out = sfa.bcast(sl, x)
+    want = np.zeros((sl.leaf_extent, bs))
+    xh = x.detach().cpu().numpy()
+    want[L] = xh[R]
+    assert np.array_equal(out.detach().cpu().numpy(), want)
+    g = torch.randint(-50, 50, out.shape, device="cuda").double()
+    out.backward(g)
+    gh = g.cpu().numpy()
+    want_g = np.zeros((sl.nroots_total, bs))
+    np.add.at(want_g, R, gh[L])
+    assert np.array_equal(x.grad.cpu().numpy(), want_g)
+
+
 def test_gradients_are_dense_transposes():
     """Bcast backward = P^T g, Reduce SUM backward = P g (fp64, exact for these sums of at most
     a few hundred terms of integer-valued data)."""

@@ -135,3 +135,30 @@ def test_autotune_choice_is_valid_and_auto_stays_correct(kind):
         sf.set_mode("auto").reduce(l, r, "SUM")
         want = oracle.reduce(f, "fp64", 1, leaf, root, "SUM")
         assert_atomic_sum_close(to_host(r, "fp64"), want, f, "fp64", 1, leaf, root, "auto reduce")
+
+
+def test_batch_rebuilds_after_a_forest_scratch_grows():
+    """A batch keeps device tables that point at each forest's fold scratch.  A later single
+    Reduce with a wider unit grows (reallocates) that scratch; the next batch run must notice
+    and rebuild, in both the plain and the graph form, and still match the oracle."""
+    f = sfgen.zipf_forest(31, 2, 40000, 500, 3)      # heavy roots: multi-block folds use the scratch
+    sf = StarForest.from_forest(f).setup().set_mode("deterministic")
+    assert sf.info()["rm_chunks"] > sf.info()["multi_roots"]
+    root, leaf = make_data(f, "fp32", 1, 1200)
+    wroot, wleaf = make_data(f, "fp64", 8, 1201)
+    for use_graph in (False, True):
+        r, l = to_dev(root, "fp32"), to_dev(leaf, "fp32")
+        b = Batch().set_ops([("reduce", sf, "SUM", l, r, 1)])
+        b.run(use_graph=use_graph)
+        torch.cuda.synchronize()
+        want = oracle.reduce(f, "fp32", 1, leaf, root, "SUM")
+        assert_bits_equal(to_host(r, "fp32"), want, "first batch run")
+        wr, wl = to_dev(wroot, "fp64"), to_dev(wleaf, "fp64")
+        sf.reduce(wl, wr, "SUM", bs=8)           # 64-byte units: the scratch is reallocated
+        torch.cuda.synchronize()
+        assert_bits_equal(to_host(wr, "fp64"), oracle.reduce(f, "fp64", 8, wleaf, wroot, "SUM"), "wide reduce")
+        r.copy_(to_dev(root, "fp32"))
+        b.run(use_graph=use_graph)
+        torch.cuda.synchronize()
+        assert_bits_equal(to_host(r, "fp32"), want, f"batch run after the scratch moved (graph={use_graph})")
+    assert sf.device_status() == 0

@@ -21,6 +21,21 @@ from paper_2102_13018_gb300 import StarForest  # noqa: E402
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig2.json")))
 
 
+@pytest.mark.parametrize("dtype,bs", [("int32", 1), ("fp32", 2), ("bf16", 3), ("int64", 1)])
+def test_gather_scatter_match_oracle(dtype, bs):
+    f = sfgen.zipf_forest(12, 3, 30000, 4000, 4)
+    sf = StarForest.from_forest(f).setup()
+    m = sf.multi_sf()
+    root, leaf = make_data(f, dtype, bs, 1402)
+    multi0 = sfgen.data(dtype, m.nroots_total * bs, 1402, 3)
+    multi = to_dev(multi0, dtype)
+    sf.gather(to_dev(leaf, dtype), multi, bs=bs)
+    assert_bits_equal(to_host(multi, dtype), oracle.gather(f, dtype, bs, leaf, multi0), f"gather {dtype}x{bs}")
+    l = to_dev(leaf, dtype)
+    sf.scatter(to_dev(multi0, dtype), l, bs=bs)
+    assert_bits_equal(to_host(l, dtype), oracle.scatter(f, dtype, bs, multi0, leaf), f"scatter {dtype}x{bs}")
+
+
 def test_fig2_multi_forest_sizes_and_gather():
     sf = StarForest.from_forest(sfgen.fig2()).setup()
     m = sf.multi_sf()
@@ -62,12 +77,13 @@ def test_gather_then_scatter_round_trip(f):
     got = to_host(back, "fp64").reshape(-1, 3)
     assert np.array_equal(got[connected], leaf.reshape(-1, 3)[connected])
     assert np.all(got[~connected] == 0)
-    # new roots of root r are its leaves in canonical order
-    mh = multi.cpu().numpy().reshape(-1, 3)
-    order = np.argsort(R, kind="stable")
-    ro_m = m.rootoff
-    # rank-major new roots: rank p holds, for its roots in order, their leaves in canonical order
-    assert np.array_equal(mh, leaf.reshape(-1, 3)[L[order]])
+    # the oracle's Gather and Scatter (Sec. III.B), element by element
+    want_multi = oracle.gather(f, "fp64", 3, leaf, np.zeros(m.nroots_total * 3))
+    assert_bits_equal(multi.cpu().numpy(), want_multi, f"gather {f.name}")
+    leaf0 = sfgen.data("fp64", leaf.size, 1401, 1)
+    back2 = to_dev(leaf0, "fp64")
+    sf.scatter(to_dev(want_multi, "fp64"), back2, bs=3)
+    assert_bits_equal(to_host(back2, "fp64"), oracle.scatter(f, "fp64", 3, want_multi, leaf0), f"scatter {f.name}")
 
 
 @pytest.mark.parametrize("f", [sfgen.cfg3_spmv(1 << 15, 4), sfgen.random_forest(62, 4, 200, 300)],

@@ -4,7 +4,8 @@ import pytest
 
 import oracle
 import sfgen
-from tests.gpu_util import assert_atomic_sum_close, assert_bits_equal, make_data, to_dev, to_host
+from tests.gpu_util import (assert_atomic_sum_close, assert_bits_equal, make_data, signed_zero_data,
+                            signed_zero_forest, to_dev, to_host)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,13 +58,16 @@ def test_bcast_bit_exact(f, path, op, dtype, bs):
 @pytest.mark.parametrize("dtype", DT)
 def test_reduce_deterministic_bit_exact(f, op, dtype):
     sf = sf_for(f).set_mode("deterministic")
+    # integers also over their full range, so SUM wraps around (two's complement)
+    kinds = ("signed", "wide") if dtype.startswith("int") else ("signed",)
     for bs in (1, 5):
-        root, leaf = make_data(f, dtype, bs, 200)
-        want = oracle.reduce(f, dtype, bs, leaf, root, op)
-        r, l = to_dev(root, dtype), to_dev(leaf, dtype)
-        sf.reduce(l, r, op, bs=bs)
-        assert_bits_equal(to_host(r, dtype), want, f"reduce det {f.name} {op} {dtype}x{bs}")
-        assert_bits_equal(to_host(l, dtype), leaf, "leafdata must be untouched")
+        for kind in kinds:
+            root, leaf = make_data(f, dtype, bs, 200, kind, kind)
+            want = oracle.reduce(f, dtype, bs, leaf, root, op)
+            r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+            sf.reduce(l, r, op, bs=bs)
+            assert_bits_equal(to_host(r, dtype), want, f"reduce det {f.name} {op} {dtype}x{bs} {kind}")
+            assert_bits_equal(to_host(l, dtype), leaf, "leafdata must be untouched")
     assert sf.device_status() == 0
 
 
@@ -71,11 +75,12 @@ def test_reduce_deterministic_bit_exact(f, op, dtype):
 @pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
 @pytest.mark.parametrize("dtype", ["int32", "int64", "fp32", "fp64"])
 def test_reduce_atomic(f, op, dtype):
-    sf = sf_for(f).set_mode("atomic")
     bs = 2
-    root, leaf = make_data(f, dtype, bs, 300)
+    kind = "wide" if dtype.startswith("int") else "signed"   # integer SUM wraps around
+    root, leaf = make_data(f, dtype, bs, 300, kind, kind)
     want = oracle.reduce(f, dtype, bs, leaf, root, op)
     r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+    sf = sf_for(f).set_mode("atomic")
     sf.reduce(l, r, op, bs=bs)
     got = to_host(r, dtype)
     sf.set_mode("deterministic")
@@ -90,7 +95,8 @@ def test_reduce_atomic(f, op, dtype):
 @pytest.mark.parametrize("dtype,bs", [("int32", 1), ("fp64", 1), ("fp32", 4), ("int64", 3)])
 def test_fetch_and_op_deterministic_bit_exact(f, op, dtype, bs):
     sf = sf_for(f).set_mode("deterministic")
-    root, leaf = make_data(f, dtype, bs, 400)
+    kind = "wide" if dtype.startswith("int") else "signed"   # integer SUM wraps around
+    root, leaf = make_data(f, dtype, bs, 400, kind, kind)
     upd0 = sfgen.data(dtype, leaf.size, 400, 3)
     want_root, want_upd = oracle.fetch_and_op(f, dtype, bs, root, leaf, upd0, op)
     r, l, u = to_dev(root, dtype), to_dev(leaf, dtype), to_dev(upd0, dtype)
@@ -286,3 +292,76 @@ def test_pingpong_round_trip_restores_roots(nbytes):
         x.zero_()
         sf.reduce(lv, x, "REPLACE")
     assert torch.equal(x, x0)
+
+
+SZ = signed_zero_forest()
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp64"])
+@pytest.mark.parametrize("op", ["MIN", "MAX"])
+@pytest.mark.parametrize("bs", [1, 3])
+def test_min_max_signed_zero_ties_bit_exact(dtype, op, bs):
+    """Deterministic MIN/MAX must keep the first of equal values in canonical order, as the
+    oracle does: +0 and -0 compare equal but differ in their bits."""
+    sf = sf_for(SZ).set_mode("deterministic")
+    root, leaf = signed_zero_data(SZ, dtype, bs, 94)
+    if op == "MIN":
+        root = np.where(root == -1.0, -root, root).astype(root.dtype)
+    want = oracle.reduce(SZ, dtype, bs, leaf, root, op)
+    assert np.signbit(want).any() and (~np.signbit(want)).any()
+    r, l = to_dev(root, dtype), to_dev(leaf, dtype)
+    sf.reduce(l, r, op, bs=bs)
+    assert_bits_equal(to_host(r, dtype), want, f"signed zeros {op} {dtype}x{bs}")
+    assert sf.device_status() == 0
+
+
+def _small_ladder():
+    f = degree_ladder(500, 2, 97)
+    f.name = "degree_ladder_500"
+    return f
+
+
+FROM_ZERO_FORESTS = FORESTS + [sfgen.owned_plus_ghosts(5), _small_ladder()]
+
+
+@pytest.mark.parametrize("f", FROM_ZERO_FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("mode", ["deterministic", "atomic"])
+@pytest.mark.parametrize("op", ["REPLACE", "SUM", "MIN", "MAX"])
+def test_reduce_from_zero_equals_reduce_into_zeros(f, mode, op):
+    """sf_reduce_from_zero = a Reduce into roots that were all zero, without reading them:
+    the root buffer starts as NaN garbage (all-ones bits for integers) here."""
+    sf = sf_for(f).set_mode(mode)
+    ro, lo = oracle.layout(f)
+    for dtype, bs in (("fp64", 1), ("fp32", 4), ("bf16", 8), ("int32", 1), ("fp32", 64)):
+        _, leaf = make_data(f, dtype, bs, 700)
+        zeros = np.zeros(int(ro[-1]) * bs, oracle.NPTYPE[dtype])
+        want = oracle.reduce(f, dtype, bs, leaf, zeros, op)
+        garbage = np.full(int(ro[-1]) * bs, 0xFFFF if dtype == "bf16" else -1, oracle.NPTYPE[dtype])
+        if dtype in ("fp32", "fp64"):
+            garbage[:] = np.nan
+        r = to_dev(garbage, dtype)
+        sf.reduce_from_zero(to_dev(leaf, dtype), r, op, bs=bs)
+        got = to_host(r, dtype)
+        if mode == "atomic" and op == "SUM" and dtype in ("fp32", "fp64"):
+            assert_atomic_sum_close(got, want, f, dtype, bs, leaf, zeros, f"from zero {f.name} {op}")
+        else:
+            assert_bits_equal(got, want, f"from zero {f.name} {mode} {op} {dtype}x{bs}")
+    sf.set_mode("deterministic")
+    assert sf.device_status() == 0
+
+
+@pytest.mark.parametrize("f", [sfgen.random_forest(44, 4, 300, 200), sfgen.owned_plus_ghosts(6, keep=0.6)],
+                         ids=lambda f: f.name)
+def test_zero_leafless_roots(f):
+    sf = sf_for(f)
+    ro, _ = oracle.layout(f)
+    deg = oracle.in_degree(f)
+    bs = 3
+    root = sfgen.data("fp32", int(ro[-1]) * bs, 710, 1)
+    arg = np.arange(int(ro[-1]) * bs, dtype=np.int32)
+    r, a = to_dev(root, "fp32"), torch.from_numpy(arg.copy()).cuda()
+    sf.zero_leafless_roots(r, a, bs=bs)
+    empty = np.repeat(deg == 0, bs)
+    assert empty.any() and (~empty).any()
+    assert_bits_equal(to_host(r, "fp32"), np.where(empty, np.float32(0), root), "leafless roots zeroed")
+    assert np.array_equal(a.cpu().numpy(), np.where(empty, -1, arg))

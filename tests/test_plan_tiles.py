@@ -1,9 +1,11 @@
 """The root-major plan's chunk tiles against the shared-memory stages of the kernels that
 read them.  The library's own setup pass (sf_setup.cpp, compiled here with g++) builds plans
 for varied forests; for both chunk-tile lists -- the general Reduce kernel's and the
-one-vector (NV1) kernel's -- every tile must fit its kernel's stage (block records and leaf
-entries, widened as the kernel widens them), describe exactly the leaf span of its blocks,
-and the tiles must cover every fold block exactly once.  CPU only."""
+one-vector (NV1) kernel's, of every root and of the roots the diagonal chunks leave out --
+every tile must fit its kernel's stage (block records and leaf entries, widened as the kernel
+widens them), describe exactly the leaf span of its blocks, and the tiles must cover every
+fold block exactly once.  The tiles of the staged diagonal-chunk Reduce are checked the same
+way: every bulk copy aligned and inside its array and its shared-memory area.  CPU only."""
 import os
 import shutil
 import subprocess
@@ -59,6 +61,96 @@ static int check_list(const HostPlan &p, const std::vector<RmTile> &tiles, int s
   return 0;
 }
 
+// The staged diagonal-chunk kernel's copies for every tile and unit width: the same spans the
+// kernel forms (dg_spans), checked to start 16-byte aligned, to stay inside the root, leaf and x
+// arrays and inside the stage's areas (leaf and x areas: the span's bytes plus 32 spare); the
+// tiles must cover every chunk that has a coded root exactly once, with one delta, at most
+// DG_TILE_CHUNKS chunks and DG_TILE_XCAP x entries, and `full` must say whether every root of
+// the tile below the last root is coded.
+static int64_t dg_tiles_checked = 0;
+static int check_dg(const HostPlan &p, int64_t NR, int64_t leaf_units, const char *name) {
+  const DiagHost &d = p.dg;
+  dg_tiles_checked += int64_t(d.tiles.size());
+  const int64_t nch = int64_t(d.chunks.size());
+  std::vector<int> seen(nch, 0);
+  for (const DgTile &t : d.tiles) {
+    if (t.n < 1 || t.n > DG_TILE_CHUNKS || t.c < 0 || t.c + t.n > nch || t.xend - t.xbeg > DG_TILE_XCAP ||
+        t.xbeg != d.chunks[t.c].xoff) {
+      std::printf("%s: bad tile c=%d n=%d x=[%d,%d)\n", name, t.c, t.n, t.xbeg, t.xend);
+      return 1;
+    }
+    bool full = true;
+    for (int32_t k = t.c; k < t.c + t.n; ++k) {
+      seen[k]++;
+      if (d.chunks[k].delta != t.delta) { std::printf("%s: tile mixes deltas\n", name); return 1; }
+      for (int lane = 0; lane < 32; ++lane) {
+        const int64_t u = (d.c0 + k) * 32 + lane;
+        const uint32_t code = ((lane < 16 ? d.chunks[k].lo : d.chunks[k].hi) >> (2 * (lane & 15))) & 3u;
+        if (u < NR && !code) full = false;
+        if (u >= NR && code) { std::printf("%s: code beyond the last root\n", name); return 1; }
+        if (code && (u + t.delta < 0 || u + t.delta >= leaf_units)) { std::printf("%s: diagonal leaf out of range\n", name); return 1; }
+      }
+    }
+    if (bool(t.full) != full) { std::printf("%s: full flag wrong\n", name); return 1; }
+    // every list root's list (a negative header, then its other leaves) inside [lbeg, lend)
+    for (int32_t k = t.c, xi = t.xbeg; k < t.c + t.n; ++k)
+      for (int lane = 0; lane < 32; ++lane) {
+        const uint32_t code = ((lane < 16 ? d.chunks[k].lo : d.chunks[k].hi) >> (2 * (lane & 15))) & 3u;
+        if (code < DG_PAIR) continue;
+        if (code == DG_LIST) {
+          const int32_t o = d.x[xi];
+          if (o < t.lbeg || o >= t.lend || d.lists[o] >= 0) { std::printf("%s: list outside its tile\n", name); return 1; }
+          const int32_t h = -1 - d.lists[o], n = (h & 0xffff) + (h >> 16);
+          if (o + 1 + n > t.lend) { std::printf("%s: list runs past its tile\n", name); return 1; }
+          for (int32_t q = 1; q <= n; ++q)
+            if (d.lists[o + q] < 0 || d.lists[o + q] >= leaf_units) { std::printf("%s: bad list entry\n", name); return 1; }
+        }
+        ++xi;
+      }
+    {
+      const int64_t lslo = (int64_t(t.lbeg) * 4) & ~int64_t(15);
+      const int64_t lshi = (int64_t(t.lend) * 4 + 15) & ~int64_t(15);
+      const bool staged = t.lend > t.lbeg && t.lend - t.lbeg <= DG_TILE_LCAP;
+      if (t.lbeg < 0 || t.lend < t.lbeg || t.lend > int64_t(d.lists.size()) ||
+          (staged && (lshi > int64_t(d.lists.size()) * 4 + 16 || lshi - lslo > DG_TILE_LCAP * 4 + 32))) {
+        std::printf("%s: list span [%d, %d) out of bounds\n", name, t.lbeg, t.lend);
+        return 1;
+      }
+    }
+    const int64_t xend_chunks = t.c + t.n < nch ? d.chunks[t.c + t.n].xoff : int64_t(d.x.size());
+    if (t.xend != xend_chunks) { std::printf("%s: tile x span is not its chunks' span\n", name); return 1; }
+    for (int VB : {2, 4, 8, 16}) {
+      const int64_t R = int64_t(DG_TILE_CHUNKS) * 32 * VB;
+      const int64_t u0 = (d.c0 + t.c) * 32;
+      const int64_t n = std::min<int64_t>(int64_t(t.n) * 32, NR - u0);
+      const int64_t rstage = (n * VB) & ~int64_t(15);
+      const int64_t L0 = u0 + t.delta, leaf_bytes = leaf_units * VB;
+      int64_t llo = std::max<int64_t>(0, (L0 * VB) & ~int64_t(15));
+      int64_t lhi = std::min<int64_t>(((L0 + n) * VB + 15) & ~int64_t(15), leaf_bytes & ~int64_t(15));
+      if (lhi < llo) lhi = llo;
+      const int64_t xlo = (int64_t(t.xbeg) * 4) & ~int64_t(15);
+      const int64_t xhi = t.xend == t.xbeg ? xlo : ((int64_t(t.xend) * 4 + 15) & ~int64_t(15));
+      const int64_t xbytes = int64_t(d.x.size()) * 4 + 16;   // the plan blob keeps 16 bytes after an array
+      const bool ok = n > 0 && rstage >= 0 && rstage <= R && u0 * VB + rstage <= NR * VB && (u0 * VB) % 16 == 0 &&
+                      llo % 16 == 0 && lhi % 16 == 0 && llo >= 0 && lhi <= leaf_bytes && lhi - llo <= R + 32 &&
+                      xlo % 16 == 0 && xhi % 16 == 0 && xhi <= xbytes && xhi - xlo <= DG_TILE_XCAP * 4 + 32 &&
+                      t.n * 16 <= DG_TILE_CHUNKS * 16;
+      if (!ok) {
+        std::printf("%s: tile c=%d VB=%d spans out of bounds (roots %lld, leaves [%lld,%lld) of %lld, x [%lld,%lld))\n",
+                    name, t.c, VB, (long long)rstage, (long long)llo, (long long)lhi, (long long)leaf_bytes,
+                    (long long)xlo, (long long)xhi);
+        return 1;
+      }
+    }
+  }
+  for (int64_t k = 0; k < nch; ++k)
+    if (seen[k] != int(bool(d.chunks[k].lo | d.chunks[k].hi))) {
+      std::printf("%s: chunk %lld covered %d times\n", name, (long long)k, seen[k]);
+      return 1;
+    }
+  return 0;
+}
+
 // forest from per-leaf global roots (ranks split evenly, ilocal identity)
 static int run(const char *name, int P, int64_t nroots_total, const std::vector<int64_t> &root_of_leaf) {
   std::vector<int64_t> nroots(P, nroots_total / P), nleaves(P, 0);
@@ -85,8 +177,13 @@ static int run(const char *name, int P, int64_t nroots_total, const std::vector<
     std::printf("%s: setup failed\n", name);
     return 1;
   }
-  return check_list(plan, plan.rm_fold_tiles, RM_STAGE_LEAVES, name) +
-         check_list(plan, plan.rm_fold_nv1_tiles, RM_STAGE_LEAVES_NV1, name);
+  int bad = check_list(plan, plan.rm_fold_tiles, RM_STAGE_LEAVES, name) +
+            check_list(plan, plan.rm_fold_nv1_tiles, RM_STAGE_LEAVES_NV1, name) +
+            check_dg(plan, info.nroots_total, info.leaf_extent_total, name);
+  if (plan.rest)   // the root-major plan of the roots the diagonal chunks leave out
+    bad += check_list(*plan.rest, plan.rest->rm_fold_tiles, RM_STAGE_LEAVES, name) +
+           check_list(*plan.rest, plan.rest->rm_fold_nv1_tiles, RM_STAGE_LEAVES_NV1, name);
+  return bad;
 }
 
 int main() {
@@ -122,11 +219,38 @@ int main() {
     for (int64_t i = int64_t(r.size()) - 1; i > 0; --i) std::swap(r[i], r[below(i + 1)]);
     bad += run("large", 8, N, r);
   }
+  {   // every root owns the leaf at its own position (diagonal chunks), plus ghosts and heavy
+      // roots of up to 9000 leaves left to the root-major plan of the rest
+    std::vector<int64_t> r;
+    const int64_t N = 600000;
+    for (int64_t k = 0; k < N; ++k) r.push_back(k);
+    for (int64_t j = 0; j < 200000; ++j) r.push_back(below(N));
+    for (int64_t h = 0; h < 30; ++h)
+      for (int64_t j = 0; j < 300 * h; ++j) r.push_back(h * 1000);
+    bad += run("diagonal", 6, N, r);
+  }
+  {   // diagonal leaves at a negative offset (leaf = root - 37) on odd-sized ranks, ghosts after
+    std::vector<int64_t> r;
+    const int64_t N = 100003;
+    for (int64_t k = 0; k < 37; ++k) r.push_back(below(N));
+    for (int64_t k = 0; k < N; ++k) r.push_back(k);
+    for (int64_t j = 0; j < 30001; ++j) r.push_back(below(N));
+    bad += run("diagonal_shifted", 7, N, r);
+  }
+  {   // negative offset (leaf = root - 37): the first roots have no diagonal leaf, so a tile's
+      // leaf span would start before the leaf array
+    std::vector<int64_t> r;
+    const int64_t N = 70001;
+    for (int64_t k = 0; k < N; ++k) r.push_back(k + 37 < N ? k + 37 : below(N));
+    for (int64_t j = 0; j < 9001; ++j) r.push_back(below(N));
+    bad += run("diagonal_negative", 3, N, r);
+  }
   {   // one-to-one: no fold blocks at all
     std::vector<int64_t> r(50000);
     for (int64_t i = 0; i < 50000; ++i) r[i] = i;
     bad += run("one_to_one", 5, 50000, r);
   }
+  if (dg_tiles_checked < 100) { std::printf("only %lld diagonal tiles\n", (long long)dg_tiles_checked); bad++; }
   std::printf("%s\n", bad ? "FAIL" : "OK");
   return bad != 0;
 }

@@ -9,8 +9,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import sfgen
-from tests.gpu_util import assert_bits_equal, make_data, to_dev, to_host
+from tests.gpu_util import assert_bits_equal, make_data, signed_zero_data, signed_zero_forest, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +30,7 @@ def heavy_forests():
     n = 150000
     star = sfgen.Forest(1, np.array([3]), np.array([n]), [None], [np.zeros(n, np.int32)],
                         [(np.arange(n) % 3).astype(np.int64)], name="star3")
-    return [star, sfgen.zipf_forest(91, 2, 60000, 2000, 4), sfgen.cfg3_spmv(1 << 15, 4)]
+    return [star, sfgen.zipf_forest(91, 2, 60000, 2000, 4), sfgen.cfg3_spmv(1 << 15, 4), sfgen.owned_plus_ghosts(5)]
 
 
 FORESTS = heavy_forests()
@@ -62,6 +63,7 @@ def test_noalloc_matches_existing_reduce_twice(f, dtype, bs, op):
     r_ref = to_dev(root, dtype)
     existing_reduce(sf, l, r_ref, unit, op)
     want = to_host(r_ref, dtype)
+    assert_bits_equal(want, oracle.reduce(f, dtype, bs, leaf, root, op), f"existing reduce vs oracle {f.name}")
     for call in range(2):           # two calls in a row share the one scratch array
         r = to_dev(root, dtype)
         assert noalloc_reduce(sf, l, r, unit, op) == 0
@@ -103,4 +105,24 @@ def test_noalloc_rejects_bad_arguments_like_reduce_begin():
     assert sf._lib.sf_reduce_noalloc(sf._h, _abi.sf_unit(9, 1), p, p, 1, None) == _abi.CODES["SF_ERR_ARG"]
     q = ctypes.c_void_p(buf.data_ptr() + 4)
     assert sf._lib.sf_reduce_noalloc(sf._h, unit, q, p, 1, None) == _abi.CODES["SF_ERR_ALIGN"]
+    sf.destroy()
+
+
+@pytest.mark.parametrize("op", ["MIN", "MAX"])
+def test_noalloc_keeps_signed_zero_ties_like_the_oracle(op):
+    """+0 and -0 compare equal: MIN/MAX must keep the first in canonical order, exactly as
+    the deterministic Reduce and the oracle do, on two calls in a row."""
+    SZ = signed_zero_forest()
+    sf = StarForest.from_forest(SZ).setup()
+    root, leaf = signed_zero_data(SZ, "fp64", 2, 95)
+    if op == "MIN":
+        root = np.where(root == -1.0, -root, root)
+    want = oracle.reduce(SZ, "fp64", 2, leaf, root, op)
+    unit = _abi.sf_unit(_abi.SF_FP64, 2)
+    l = to_dev(leaf, "fp64")
+    for call in range(2):
+        r = to_dev(root, "fp64")
+        assert noalloc_reduce(sf, l, r, unit, op) == 0
+        torch.cuda.synchronize()
+        assert_bits_equal(to_host(r, "fp64"), want, f"noalloc signed zeros {op} call {call}")
     sf.destroy()
