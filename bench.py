@@ -266,7 +266,11 @@ def run_reference(args):
 def run_batched(args, stream, flush):
     """512 uneven forests (Zipf in-degree, mixed dtype / bs / op), each doing one Bcast and one
     Reduce: one library call per forest and operation vs one batched run (variant-grouped
-    launches) vs the batched run replayed as one CUDA graph."""
+    launches) vs the batched run replayed as one CUDA graph -- first with every Reduce
+    deterministic and the default launch shapes, then with every forest tuned on its own
+    (sf_autotune: Bcast path x vector width x tile size, Reduce mode x vector width x tile size;
+    a Reduce the tuner sends to atomics is no longer bit-reproducible)."""
+    import collections
     import numpy as np
     import torch
     import sfgen
@@ -296,8 +300,6 @@ def run_batched(args, stream, flush):
         for sf, op, r, l, r2, l2, bs in items:
             sf.reduce(l2, r2, op, bs=bs, stream=stream)
 
-    batch = Batch().set_ops(ops)
-
     def timed(fn, reps=5):
         for _ in range(2):
             fn()
@@ -313,16 +315,35 @@ def run_batched(args, stream, flush):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    t_per = timed(per_forest)
-    t_batch = timed(lambda: batch.run(use_graph=False, stream=stream))
-    t_graph = timed(lambda: batch.run(use_graph=True, stream=stream))
+    def measure():
+        batch = Batch().set_ops(ops)
+        t_per = timed(per_forest)
+        t_batch = timed(lambda: batch.run(use_graph=False, stream=stream))
+        t_graph = timed(lambda: batch.run(use_graph=True, stream=stream))
+        return {"per_forest_ms": t_per, "batched_ms": t_batch, "graph_ms": t_graph,
+                "launches_batched": batch.launches(), "per_forest_gbs": nbytes / (t_per * 1e-3) / 1e9,
+                "batched_gbs": nbytes / (t_batch * 1e-3) / 1e9, "graph_gbs": nbytes / (t_graph * 1e-3) / 1e9,
+                "speedup_graph_vs_per_forest": t_per / t_graph}
+
+    det = measure()
+    t0 = time.perf_counter()
+    for sf, op, r, l, r2, l2, bs in items:
+        sf.set_mode("auto").set_path("auto")
+        sf.autotune("bcast", r, l, op, bs=bs, stream=stream)
+        sf.autotune("reduce", l2, r2, op, bs=bs, stream=stream)
+    tune_s = time.perf_counter() - t0
+    tuned = measure()
+    choices = collections.Counter()
+    for sf, *_ in items:
+        t = sf.tuning()
+        choices[f"{t['path']}/{t['mode']}/vec{t['vector_bytes']}/tile{t['tile_edges']}"] += 1
+    tuned.update({"tuning_s": tune_s, "choices": dict(choices.most_common())})
     return {"workload": f"{len(items)} forests, nleaves log-uniform in [1e2,1e6], Zipf(1.1) in-degree, "
                         f"fp32/fp64/int64, bs in {{1,2,3,8}}, op in {{SUM,MAX,REPLACE}}; Bcast then Reduce each",
-            "edges": int(edges), "algorithmic_bytes": int(nbytes),
-            "per_forest_ms": t_per, "batched_ms": t_batch, "graph_ms": t_graph,
-            "launches_per_forest_path": 2 * len(items), "launches_batched": batch.launches(),
-            "per_forest_gbs": nbytes / (t_per * 1e-3) / 1e9, "batched_gbs": nbytes / (t_batch * 1e-3) / 1e9,
-            "graph_gbs": nbytes / (t_graph * 1e-3) / 1e9, "speedup_graph_vs_per_forest": t_per / t_graph}
+            "edges": int(edges), "algorithmic_bytes": int(nbytes), "launches_per_forest_path": 2 * len(items),
+            "deterministic": det, "tuned": tuned,
+            # the headline figures: the deterministic batch (results bit-identical to the oracle)
+            "per_forest_ms": det["per_forest_ms"], "graph_ms": det["graph_ms"], "graph_gbs": det["graph_gbs"]}
 
 
 def run_tiny(stream):
@@ -741,9 +762,10 @@ def main():
     value = job_value(bb + rb, K, max_ms, world)
     peak, peak_src = measured_peak()
     b_avg, r_avg = statistics.mean(bcast_ms), statistics.mean(reduce_ms)
-    # the deterministic Reduce is one launch: the diagonal-chunk kernel when the plan covers
-    # every connected root, else the root-major kernel
-    rk = "dg_kernel" if info["dg_chunks"] > 0 and info["dg_rest_roots"] == 0 else "rm_kernel"
+    # the deterministic Reduce is one launch of its plan's kernel (a diagonal plan that leaves
+    # roots out adds a root-major launch for them)
+    plan = sf.tuning()["reduce_plan"]
+    rk = {"root_major": "rm_kernel", "diagonal": "dg_kernel", "diagonal_staged": "dg_bulk_kernel"}[plan]
     dom = (rk, rb, r_avg) if r_avg >= b_avg else ("ts_kernel", bb, b_avg)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom[0] + (" (Reduce SUM, deterministic)" if dom[0] != "ts_kernel"
@@ -769,6 +791,12 @@ def main():
             ms = time_op(lambda: sf.reduce(lvec, y, "SUM", stream=stream), stream, flush)
             variants[f"reduce_sum_{mode}"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
         sf.set_mode("deterministic")
+        if info["dg_chunks"] > 0:
+            for p in ("diagonal", "diagonal_staged"):
+                sf.set_reduce_plan(p)
+                ms = time_op(lambda: sf.reduce(lvec, y, "SUM", stream=stream), stream, flush)
+                variants[f"reduce_sum_deterministic_{p}"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}
+            sf.set_reduce_plan("auto")
         ms = time_op(lambda: sf._lib.sf_reduce_noalloc(sf._h, sf._unit(y, sf.nroots_total, None),
                                                       sf._ptr(lvec), sf._ptr(y), 1, sf._stream(stream)), stream, flush)
         variants["reduce_sum_noalloc"] = {"ms": ms, "gbs": rb / (ms * 1e-3) / 1e9}

@@ -85,6 +85,15 @@ enum { SF_MODE_AUTO = 0, SF_MODE_ATOMIC = 1, SF_MODE_DETERMINISTIC = 2 };
  * AUTO: the library picks (FUSED, or what sf_autotune measured fastest). */
 enum { SF_PATH_AUTO = 0, SF_PATH_FUSED = 1, SF_PATH_THREE_PHASE = 2, SF_PATH_ROOT_MAJOR = 3 };
 
+/* Plans of the deterministic Reduce of one-vector units (SUM/MIN/MAX; results are identical):
+ * ROOT_MAJOR: CSR-by-root fold tiles with a two-level combine for roots that span tiles.
+ * DIAGONAL: 32-root chunks whose roots take their first leaf at one common offset (Sec. V.B's
+ *   contiguous patterns, per chunk), then the root-major plan of the roots left out; only on
+ *   forests where the setup pass found such chunks (sf_info.dg_chunks > 0).
+ * DIAGONAL_STAGED: DIAGONAL with each tile's spans staged in shared memory by bulk copies.
+ * AUTO: ROOT_MAJOR, or what sf_autotune measured fastest. */
+enum { SF_PLAN_AUTO = 0, SF_PLAN_ROOT_MAJOR = 1, SF_PLAN_DIAGONAL = 2, SF_PLAN_DIAGONAL_STAGED = 3 };
+
 /* Where data lives, for the *_with_memtype calls (PetscSFBcastWithMemTypeBegin, Sec. V.C). */
 enum { SF_MEM_HOST = 0, SF_MEM_DEVICE = 1 };
 
@@ -167,6 +176,30 @@ int sf_get_info(const sf_t *sf, sf_info *info);
 /* Select the Reduce mode (SF_MODE_*) and the Bcast data path (SF_PATH_*). */
 int sf_set_mode(sf_t *sf, int32_t mode);
 int sf_set_path(sf_t *sf, int32_t path);
+/* Select the deterministic Reduce plan (SF_PLAN_*); a forest without diagonal chunks runs
+ * ROOT_MAJOR whatever is set. */
+int sf_set_reduce_plan(sf_t *sf, int32_t plan);
+
+/* Launch shape of the forest's kernels (the choices sf_autotune makes; results do not change):
+ * vector_bytes caps the vector each thread moves per unit access (2, 4, 8 or 16; 0 = 16; a unit's
+ * element size is always allowed), and tile_edges sets the edges per CTA tile of the two-sided
+ * kernels (fused Bcast, atomic Reduce): a power of two in [64, 65536], 0 = the setup pass's
+ * choice (sf_info.ts_tile_edges).  sf_set_tile_edges rebuilds that tile list on the device: it
+ * needs sf_setup, allocates, synchronises the device and refuses (SF_ERR_PENDING) while a Begin
+ * has no End. */
+int sf_set_vector_bytes(sf_t *sf, int32_t bytes);
+int sf_set_tile_edges(sf_t *sf, int32_t edges);
+
+typedef struct {
+  int32_t path;          /* SF_PATH_* the Bcast runs (AUTO resolved) */
+  int32_t mode;          /* SF_MODE_* the Reduce runs (AUTO resolved) */
+  int32_t vector_bytes;  /* 0 = 16 */
+  int32_t tile_edges;    /* edges per two-sided tile */
+  int32_t reduce_plan;   /* SF_PLAN_* the deterministic Reduce runs (AUTO resolved) */
+} sf_tuning;
+
+/* The forest's current choices (after sf_autotune, or as set). */
+int sf_get_tuning(const sf_t *sf, sf_tuning *out);
 
 /* Bcast (Sec. III.B): for every edge, leafdata[leaf] = op(leafdata[leaf], rootdata[root]).
  * Begin enqueues the work on `stream` (all of it for FUSED/ROOT_MAJOR; pack, self scatter and
@@ -308,11 +341,15 @@ int sf_batch_run(sf_batch_t *batch, const sf_batch_op ops[], int32_t n, int32_t 
 int sf_batch_launches(const sf_batch_t *batch, int32_t *launches);
 int sf_batch_destroy(sf_batch_t *batch);
 
-/* Autotuner: times each data path of Bcast (kind SF_OP_BCAST) or each Reduce mode (kind
- * SF_OP_REDUCE) on this forest, unit and op, `reps` times after one warm-up, writing into a
- * scratch copy of dst (src and dst are not modified), and makes the fastest the meaning of
- * SF_PATH_AUTO / SF_MODE_AUTO for the forest.  *choice (may be NULL) receives it.  Allocates
- * and synchronises `stream`.  Choosing SF_MODE_ATOMIC trades bit-reproducibility for speed. */
+/* Autotuner: times the variants of Bcast (kind SF_OP_BCAST: data path x vector width x two-sided
+ * tile size) or of Reduce (kind SF_OP_REDUCE: mode x vector width, the plan for the
+ * deterministic mode and the tile size for the atomic mode) on this forest, unit and op, `reps` times after one warm-up, writing into a
+ * scratch copy of dst (src and dst are not modified), and keeps the fastest: its path or mode
+ * becomes what SF_PATH_AUTO / SF_MODE_AUTO mean for the forest, its vector width and tile size
+ * are set (sf_set_vector_bytes, sf_set_tile_edges).  *choice (may be NULL) receives the path or
+ * mode; sf_get_tuning gives the rest, and a tuned plan becomes what SF_PLAN_AUTO means.  Allocates and synchronises.  Choosing SF_MODE_ATOMIC
+ * trades bit-reproducibility for speed; pass SF_MODE_DETERMINISTIC as the forest's mode before
+ * tuning, and the Reduce keeps it (only the vector width is tuned). */
 int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst, int32_t op, int32_t reps,
                 sf_stream_t stream, int32_t *choice);
 

@@ -13,6 +13,7 @@ SF_INT32, SF_INT64, SF_FP32, SF_FP64, SF_BF16 = range(5)
 SF_REPLACE, SF_SUM, SF_MIN, SF_MAX = range(4)
 SF_MODE_AUTO, SF_MODE_ATOMIC, SF_MODE_DETERMINISTIC = range(3)
 SF_PATH_AUTO, SF_PATH_FUSED, SF_PATH_THREE_PHASE, SF_PATH_ROOT_MAJOR = range(4)
+SF_PLAN_AUTO, SF_PLAN_ROOT_MAJOR, SF_PLAN_DIAGONAL, SF_PLAN_DIAGONAL_STAGED = range(4)
 SF_MEM_HOST, SF_MEM_DEVICE = 0, 1
 SF_OP_BCAST, SF_OP_REDUCE, SF_OP_BARRIER = 0, 1, 2
 SF_FOLD_BLOCK = 64
@@ -46,6 +47,11 @@ class sf_unit(ctypes.Structure):
 class sf_batch_op(ctypes.Structure):
     _fields_ = [("sf", ctypes.c_void_p), ("kind", ctypes.c_int32), ("unit", sf_unit), ("op", ctypes.c_int32),
                 ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p)]
+
+
+class sf_tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("mode", ctypes.c_int32), ("vector_bytes", ctypes.c_int32),
+                ("tile_edges", ctypes.c_int32), ("reduce_plan", ctypes.c_int32)]
 
 
 class sf_info(ctypes.Structure):
@@ -91,6 +97,10 @@ def load():
     lib.sf_get_info.argtypes = [vp, P(sf_info)]
     lib.sf_set_mode.argtypes = [vp, i32]
     lib.sf_set_path.argtypes = [vp, i32]
+    lib.sf_set_reduce_plan.argtypes = [vp, i32]
+    lib.sf_set_vector_bytes.argtypes = [vp, i32]
+    lib.sf_set_tile_edges.argtypes = [vp, i32]
+    lib.sf_get_tuning.argtypes = [vp, P(sf_tuning)]
     lib.sf_zero_leafless_roots.argtypes = [vp, sf_unit, vp, vp, vp]
     for name in ("sf_bcast_begin", "sf_bcast_end", "sf_reduce_begin", "sf_reduce_end", "sf_reduce_from_zero_begin",
                  "sf_reduce_from_zero_end"):

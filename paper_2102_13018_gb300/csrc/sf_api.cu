@@ -60,10 +60,10 @@ struct BlobBuilder {
 };
 
 // widest vector (bytes) usable for a unit of `ub` bytes with the given pointers
-int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs) {
+int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs, int cap) {
   static const int cand[] = {16, 8, 4, 2};
   for (int vb : cand) {
-    if (vb < w || ub % vb) continue;
+    if (vb < w || ub % vb || (vb > cap && vb > w)) continue;
     if (vb != w && !allow_wide) continue;
     bool ok = true;
     for (const void *p : ptrs)
@@ -158,7 +158,7 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
   if (sf->info.nedges == 0) return SF_SUCCESS;
   const bool copy = op == SF_REPLACE;
   if (path == SF_PATH_ROOT_MAJOR) {
-    const int vb = pick_vb(w, ub, true, {root, leaf});
+    const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
     if (!vb) return SF_ERR_ALIGN;
     const int vbo = copy ? vb : (vb == 16 ? 16 : w);
     RmArgs a = rm_args(sf, sf->dp.rm_fold_tiles, sf->dp.n_rm_fold_tiles, const_cast<void *>(root), leaf, nullptr, ub / vbo);
@@ -184,7 +184,7 @@ int bcast_launch(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32
     *finish = 1;
     return SF_SUCCESS;
   }
-  const int vb = pick_vb(w, ub, true, {root, leaf});
+  const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = copy ? vb : (vb == 16 ? 16 : w);
   TsArgs a = ts_args(sf, sf->dp.ts_tiles, sf->dp.n_ts_tiles, root, leaf, nullptr, ub / vbo, PH_FUSED);
@@ -224,9 +224,9 @@ int reduce_det_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, 
     DgArgs g = dg_args(sf, leaf, root);
     g.zero_root = zero_root;
     int rc;
-    // staged by bulk copies when both bases are 16-byte aligned, else direct loads
+    // staged by bulk copies (SF_PLAN_DIAGONAL_STAGED, both bases 16-byte aligned), else direct loads
     cudaError_t e = cudaErrorNotSupported;
-    if (sf->dp.n_dg_tiles > 0 && (reinterpret_cast<uintptr_t>(root) & 15) == 0 &&
+    if (reduce_plan(sf) == SF_PLAN_DIAGONAL_STAGED && sf->dp.n_dg_tiles > 0 && (reinterpret_cast<uintptr_t>(root) & 15) == 0 &&
         (reinterpret_cast<uintptr_t>(leaf) & 15) == 0) {
       DgBulkArgs b{g, sf->dp.dg_tiles, sf->dp.n_dg_tiles, static_cast<int32_t *>(sf->status.p),
                    sf->info.nroots_total * vbo, sf->info.leaf_extent_total * vbo};
@@ -271,7 +271,7 @@ int reduce_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int3
   }
   int rc;
   if (from_zero && (rc = zero_leafless(sf, u, root, nullptr, s))) return rc;
-  const int vb = pick_vb(w, ub, true, {root, leaf});
+  const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
   if (!vb) return SF_ERR_ALIGN;
   const int vbo = op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
   const int nv = ub / vbo;
@@ -309,9 +309,9 @@ bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op) {
   if (reduce_mode(sf) == SF_MODE_ATOMIC) return true;
   // Only integer results are independent of the arrival order: a floating MIN/MAX keeps the
   // first of two equal values (+0 and -0 compare equal), so it stays on the ordered fold.  A
-  // forest with diagonal chunks streams its roots faster than atomics reach them.
+  // Reduce set to the diagonal chunks runs there.
   const bool integer = dtype == SF_INT32 || dtype == SF_INT64;
-  return integer && sf->info.max_in_degree <= kOrderFreeMaxDegree && sf->dp.dg_nchunks == 0;
+  return integer && sf->info.max_in_degree <= kOrderFreeMaxDegree && reduce_plan(sf) == SF_PLAN_ROOT_MAJOR;
 }
 
 int ensure_ready(const sf_t *sf) {
@@ -411,6 +411,8 @@ int sf_setup(sf_t *sf, sf_stream_t stream) {
   d.ts_remote_tiles = reinterpret_cast<const TsTile *>(base + o_tsr);
   d.segs = reinterpret_cast<const SegCopy *>(base + o_segs);
   d.n_ts_tiles = int32_t(h.ts_tiles.size());
+  sf->ts_default = d.ts_tiles;
+  sf->n_ts_default = d.n_ts_tiles;
   d.n_ts_self_tiles = int32_t(h.ts_self_tiles.size());
   d.n_ts_remote_tiles = int32_t(h.ts_remote_tiles.size());
   d.n_segs = int32_t(h.segs.size());
@@ -504,6 +506,57 @@ int sf_set_path(sf_t *sf, int32_t path) {
   if (!sf) return SF_ERR_NULL;
   if (path < SF_PATH_AUTO || path > SF_PATH_ROOT_MAJOR) return SF_ERR_ARG;
   sf->path = path;
+  return SF_SUCCESS;
+}
+
+int sf_set_reduce_plan(sf_t *sf, int32_t plan) {
+  if (!sf) return SF_ERR_NULL;
+  if (plan < SF_PLAN_AUTO || plan > SF_PLAN_DIAGONAL_STAGED) return SF_ERR_ARG;
+  sf->plan = plan;
+  return SF_SUCCESS;
+}
+
+int sf_set_vector_bytes(sf_t *sf, int32_t bytes) {
+  if (!sf) return SF_ERR_NULL;
+  if (bytes != 0 && bytes != 2 && bytes != 4 && bytes != 8 && bytes != 16) return SF_ERR_ARG;
+  sf->vec_bytes = bytes;
+  return SF_SUCCESS;
+}
+
+int sf_set_tile_edges(sf_t *sf, int32_t edges) {
+  if (!sf) return SF_ERR_NULL;
+  if (!sf->setup) return SF_ERR_STATE;
+  if (!sf->pending.empty()) return SF_ERR_PENDING;
+  if (edges != 0 && (edges < 64 || edges > (1 << 16) || (edges & (edges - 1)))) return SF_ERR_ARG;
+  if (edges == sf->tile_edges) return SF_SUCCESS;
+  // work already enqueued may still read the current list
+  if (cudaDeviceSynchronize() != cudaSuccess) return SF_ERR_CUDA;
+  release(sf->ts_tuned);
+  sf->dp.ts_tiles = sf->ts_default;
+  sf->dp.n_ts_tiles = sf->n_ts_default;
+  sf->tile_edges = 0;
+  if (edges == 0) return SF_SUCCESS;
+  std::vector<TsTile> tiles;
+  cut_ts_tiles(sf->hp, edges, tiles);
+  const size_t bytes = std::max<size_t>(tiles.size() * sizeof(TsTile), 256);
+  int rc;
+  if ((rc = ensure(sf->ts_tuned, bytes, false, nullptr))) return rc;
+  if (!tiles.empty() &&
+      cudaMemcpy(sf->ts_tuned.p, tiles.data(), tiles.size() * sizeof(TsTile), cudaMemcpyHostToDevice) != cudaSuccess)
+    return SF_ERR_CUDA;
+  sf->dp.ts_tiles = static_cast<const TsTile *>(sf->ts_tuned.p);
+  sf->dp.n_ts_tiles = int32_t(tiles.size());
+  sf->tile_edges = edges;
+  return SF_SUCCESS;
+}
+
+int sf_get_tuning(const sf_t *sf, sf_tuning *out) {
+  if (!sf || !out) return SF_ERR_NULL;
+  out->path = bcast_path(sf);
+  out->mode = reduce_mode(sf);
+  out->vector_bytes = sf->vec_bytes;
+  out->tile_edges = sf->tile_edges ? sf->tile_edges : int32_t(sf->info.ts_tile_edges);
+  out->reduce_plan = reduce_plan(sf);
   return SF_SUCCESS;
 }
 
@@ -722,6 +775,7 @@ int sf_destroy(sf_t *sf) {
     release(sf->stage_root);
     release(sf->stage_leaf);
     release(sf->status);
+    release(sf->ts_tuned);
   }
   delete sf;
   return SF_SUCCESS;

@@ -39,9 +39,14 @@ bool same_ops(const std::vector<sf_batch_op> &a, const sf_batch_op *b, int32_t n
 struct sf_batch_s {
   std::vector<sf_batch_op> ops;    // the list the device tables were built for
   std::vector<int32_t> modes, paths;   // forests' resolved choices at build time
-  // every forest's fold scratch (partial, counter) as the tables captured it: a later
-  // operation on one of the forests may reallocate it, and the tables must then be rebuilt
-  std::vector<std::pair<const void *, const void *>> scratch;
+  // what the tables captured of every forest -- fold scratch (a later operation may reallocate
+  // it), two-sided tile list, vector width and Reduce plan (sf_set_tile_edges,
+  // sf_set_vector_bytes, sf_set_reduce_plan): a change rebuilds the tables
+  struct Captured {
+    const void *partial, *counter, *ts_tiles;
+    int32_t vec_bytes, plan;
+  };
+  std::vector<Captured> scratch;
   DevBuf tables;
   const TsArgs *ts_ops = nullptr;
   const RmArgs *rm_ops = nullptr;
@@ -94,7 +99,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
     if (o.kind == SF_OP_BCAST) {
       const int path = bcast_path(sf);
       paths[i] = path;
-      const int vb = pick_vb(w, ub, true, {root, leaf});
+      const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
       if (!vb) return SF_ERR_ALIGN;
       const int vbo = o.op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
       if (path == SF_PATH_ROOT_MAJOR) {
@@ -121,7 +126,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
         auto &g = grouped[{stage, 0, o.unit.dtype, o.op, w, 0, 1, 1}];
         for (int32_t t = 0; t < sf->dp.n_ts_tiles; ++t) g.push_back(BatchTile{idx, 0, sf->dp.ts_tiles + t});
       } else {
-        const int vb = pick_vb(w, ub, true, {root, leaf});
+        const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
         if (!vb) return SF_ERR_ALIGN;
         const int vbo = o.op == SF_REPLACE ? vb : (vb == 16 ? 16 : w);
         const int nv = ub / vbo;
@@ -208,9 +213,12 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
   b->ops.assign(ops, ops + n);
   b->modes = modes;
   b->paths = paths;
-  b->scratch.assign(n, {nullptr, nullptr});
+  b->scratch.assign(n, {nullptr, nullptr, nullptr, 0, 0});
   for (int32_t i = 0; i < n; ++i)
-    if (ops[i].kind != SF_OP_BARRIER) b->scratch[i] = {ops[i].sf->partial.p, ops[i].sf->counter.p};
+    if (ops[i].kind != SF_OP_BARRIER) {
+      const sf_t *sf = ops[i].sf;
+      b->scratch[i] = {sf->partial.p, sf->counter.p, sf->dp.ts_tiles, sf->vec_bytes, reduce_plan(sf)};
+    }
   return SF_SUCCESS;
 }
 
@@ -237,7 +245,10 @@ bool choices_changed(const sf_batch_t *b) {
     if (o.kind == SF_OP_BARRIER) continue;
     if (o.kind == SF_OP_BCAST && bcast_path(o.sf) != b->paths[i]) return true;
     if (o.kind == SF_OP_REDUCE && reduce_mode(o.sf) != b->modes[i]) return true;
-    if (b->scratch[i].first != o.sf->partial.p || b->scratch[i].second != o.sf->counter.p) return true;
+    const auto &c = b->scratch[i];
+    if (c.partial != o.sf->partial.p || c.counter != o.sf->counter.p || c.ts_tiles != o.sf->dp.ts_tiles ||
+        c.vec_bytes != o.sf->vec_bytes || c.plan != reduce_plan(o.sf))
+      return true;
   }
   return false;
 }
@@ -305,8 +316,8 @@ int sf_batch_destroy(sf_batch_t *b) {
   return SF_SUCCESS;
 }
 
-// Time the candidate data paths (Bcast) or modes (Reduce) on a scratch copy of the output and
-// keep the fastest as what SF_PATH_AUTO / SF_MODE_AUTO mean for this forest.
+// Time the candidate variants of Bcast or Reduce on a scratch copy of the output and keep the
+// fastest: path or mode (what AUTO means), vector width and two-sided tile size.
 int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst, int32_t op, int32_t reps,
                 sf_stream_t stream, int32_t *choice) {
   int rc;
@@ -316,26 +327,54 @@ int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst
   if (kind != SF_OP_BCAST && kind != SF_OP_REDUCE) return SF_ERR_ARG;
   if (reps < 1) reps = 3;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t ub = size_t(elem_size(unit.dtype)) * unit.bs;
+  const int w = elem_size(unit.dtype);
+  const size_t ub = size_t(w) * unit.bs;
   const size_t bytes = ub * size_t(kind == SF_OP_BCAST ? sf->info.leaf_extent_total : sf->info.nroots_total);
+  struct Cand {
+    int32_t c, vec, edges;   // path or mode, vector bytes, tile edges (0: setup's)
+    int32_t plan;            // deterministic Reduce plan
+  };
+  std::vector<Cand> cands;
+  std::vector<int32_t> vecs = {0};
+  if (ub % 16 == 0 && w < 16) vecs.push_back(w);           // 16-byte vectors or single elements
+  else if (ub % 8 == 0 && w < 8) vecs.push_back(w);
+  const int32_t sizes[] = {0, 512, 1024, 2048, 4096};
+  const int32_t plan0 = sf->plan;
+  if (kind == SF_OP_BCAST) {
+    for (int32_t v : vecs) {
+      for (int32_t e : sizes) cands.push_back({SF_PATH_FUSED, v, e, plan0});
+      cands.push_back({SF_PATH_ROOT_MAJOR, v, 0, plan0});
+      cands.push_back({SF_PATH_THREE_PHASE, v, 0, plan0});
+    }
+  } else {
+    const bool fixed = sf->mode == SF_MODE_DETERMINISTIC || op == SF_REPLACE || unit.dtype == SF_BF16;
+    // the diagonal plans serve one-vector units of SUM/MIN/MAX on forests with diagonal chunks
+    std::vector<int32_t> plans = {plan0};
+    if (plan0 == SF_PLAN_AUTO && sf->dp.dg_nchunks > 0 && op != SF_REPLACE)
+      plans = {SF_PLAN_ROOT_MAJOR, SF_PLAN_DIAGONAL, SF_PLAN_DIAGONAL_STAGED};
+    for (int32_t v : vecs)
+      for (int32_t p : plans) cands.push_back({SF_MODE_DETERMINISTIC, v, sf->tile_edges, p});
+    if (!fixed)
+      for (int32_t e : sizes) cands.push_back({SF_MODE_ATOMIC, 0, e, plan0});
+  }
   DevBuf scratch;
   if ((rc = ensure(scratch, std::max<size_t>(bytes, 256), false, s))) return rc;
-  std::vector<int32_t> cands;
-  if (kind == SF_OP_BCAST) cands = {SF_PATH_FUSED, SF_PATH_ROOT_MAJOR, SF_PATH_THREE_PHASE};
-  else if (op == SF_REPLACE || unit.dtype == SF_BF16) cands = {SF_MODE_DETERMINISTIC};
-  else cands = {SF_MODE_DETERMINISTIC, SF_MODE_ATOMIC};
   cudaEvent_t e0, e1;
   if ((rc = cuda_err(cudaEventCreate(&e0)))) { release(scratch); return rc; }
   if ((rc = cuda_err(cudaEventCreate(&e1)))) { cudaEventDestroy(e0); release(scratch); return rc; }
+  const int32_t vec0 = sf->vec_bytes, edges0 = sf->tile_edges;
   float best = 1e30f;
-  int32_t best_c = cands[0];
-  for (int32_t c : cands) {
+  Cand best_c = cands[0];
+  for (const Cand &c : cands) {
+    sf->vec_bytes = c.vec;
+    sf->plan = c.plan;
+    if ((rc = sf_set_tile_edges(sf, c.edges))) break;
     float total = 0.f;
     for (int r = 0; r <= reps && !rc; ++r) {   // first round warms up
       if (bytes) rc = cuda_err(cudaMemcpyAsync(scratch.p, dst, bytes, cudaMemcpyDeviceToDevice, s));
       if (!rc) rc = cuda_err(cudaEventRecord(e0, s));
-      if (!rc) rc = kind == SF_OP_BCAST ? bcast_all(sf, unit, src, scratch.p, op, s, c)
-                                        : reduce_all(sf, unit, src, scratch.p, op, s, c);
+      if (!rc) rc = kind == SF_OP_BCAST ? bcast_all(sf, unit, src, scratch.p, op, s, c.c)
+                                        : reduce_all(sf, unit, src, scratch.p, op, s, c.c);
       if (!rc) rc = cuda_err(cudaEventRecord(e1, s));
       if (!rc) rc = cuda_err(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -351,10 +390,19 @@ int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   release(scratch);
-  if (rc) return rc;
-  if (kind == SF_OP_BCAST) sf->tuned_path = best_c;
-  else sf->tuned_mode = best_c;
-  if (choice) *choice = best_c;
+  sf->vec_bytes = vec0;
+  sf->plan = plan0;
+  if (rc) {
+    sf_set_tile_edges(sf, edges0);
+    return rc;
+  }
+  sf->vec_bytes = best_c.vec;
+  if ((rc = sf_set_tile_edges(sf, best_c.edges))) return rc;
+  if (kind == SF_OP_BCAST) sf->tuned_path = best_c.c;
+  else sf->tuned_mode = best_c.c;
+  if (kind == SF_OP_REDUCE && best_c.c == SF_MODE_DETERMINISTIC && plan0 == SF_PLAN_AUTO && best_c.plan != SF_PLAN_AUTO)
+    sf->tuned_plan = best_c.plan;
+  if (choice) *choice = best_c.c;
   return SF_SUCCESS;
 }
 

@@ -66,4 +66,7 @@ int build_graph_extents(int32_t nranks, const int64_t nroots[], const int64_t nl
 // The setup pass: two-sided grouping, pattern detection, root-major plan, statistics.
 int analyze(const Graph &g, HostPlan &plan, sf_info &info);
 
+// The two-sided tiles of every run of the plan, `per` edges each (sf_set_tile_edges).
+void cut_ts_tiles(const HostPlan &plan, int32_t per, std::vector<TsTile> &out);
+
 }  // namespace sfgb

@@ -300,7 +300,7 @@ __device__ __forceinline__ void ts_tile(const TsArgs &a, const TsTile &t) {
     const int32_t *sidx = (L2R ? a.lidx : a.ridx) + t.idx0 + t.k0;
     const int32_t *didx = (L2R ? a.ridx : a.lidx) + t.idx0 + t.k0;
     const int32_t sb = s0 + t.k0, db = d0 + t.k0;
-    constexpr int UG = VB >= 16 ? 2 : 4;
+    constexpr int UG = 4;   // 16-byte kernels run 2 CTAs per SM: registers for 4 in flight
     for (int32_t base = threadIdx.x; base < work; base += kThreads * UG) {
       int32_t su[UG], du[UG], vv[UG];
 #pragma unroll
@@ -670,7 +670,7 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
                                            const Block b, int32_t v, bool zr = false) {
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
-  constexpr int U = VB >= 16 ? 2 : 4;
+  constexpr int U = 4;   // 16-byte kernels run 2 CTAs per SM: registers for 4 leaves in flight
   const int64_t ri = int64_t(b.root) * nv + v;
   const int32_t *lidx = m_leaf + (b.e0 - lofs);   // m_leaf holds entries from lofs on
   if constexpr (MODE == RM_BCAST) {
@@ -731,10 +731,11 @@ __device__ __forceinline__ void fold_block(void *root, void *leaf, const int32_t
 // Asynchronous global -> shared copy of one VB-byte vector (cp.async: the data goes to shared
 // memory without passing through registers, so a thread can keep many in flight).  Both
 // addresses are VB-aligned; completion is awaited with cp_async_wait_all.
+// The copy itself needs no compiler memory barrier: nothing may read its destination before
+// the cp.async.wait that follows it, and that wait is one.
 template <int VB> __device__ __forceinline__ void cp_async_vec(void *dst_smem, const void *src) {
   static_assert(VB == 4 || VB == 8 || VB == 16, "cp.async copies 4, 8 or 16 bytes");
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(VB)
-               : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(VB));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -745,7 +746,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // RM_FLAT_BYTES at a time -- and each thread folds its blocks from shared memory, entry by
 // entry in canonical order (the same left fold as fold_block), carrying the accumulators
 // across rounds.  Every thread of the CTA calls this.
-template <typename T, int VB, int OP>
+template <typename T, int VB, int OP, bool ZR>
 __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t, const BlockRec *s_rec, int32_t r0,
                                                const int32_t *s_leaf, int32_t l0, Pack<T, VB> *s_val) {
   using A = typename Acc<T, OP>::type;
@@ -760,7 +761,7 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
 #pragma unroll
   for (int j = 0; j < NBT; ++j) {
     const int32_t w = threadIdx.x + j * kThreads;
-    if (w < t.cnt && rec[w].who >= 0) xr[j] = ld_root<T, VB>(a.root, rec[w].who, a.zero_root);   // single-block root
+    if (w < t.cnt && rec[w].who >= 0) xr[j] = ld_root<T, VB>(a.root, rec[w].who, ZR);   // single-block root
   }
   for (int32_t q0 = 0; q0 < nE; q0 += R) {
     const int32_t nq = min(R, nE - q0);
@@ -788,7 +789,7 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
     const int32_t w = threadIdx.x + j * kThreads;
     if (w < t.cnt) {
       const Block b = load_block(rec, a.combs, w);
-      fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, 1, b, 0, acc[j], xr[j], a.zero_root);
+      fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, 1, b, 0, acc[j], xr[j], ZR);
     }
   }
 }
@@ -842,9 +843,12 @@ __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t 
 
 // NV1: the launch has one vector per unit (a.nv == 1; Reduce SUM/MIN/MAX with VB >= 4 only),
 // so the multi-vector fold code is left out and the kernel fits a smaller register budget.
-template <typename T, int VB, int OP, int MODE, bool NV1 = false>
+// ZR: a Reduce from zero (RmArgs.zero_root set; the roots count as 0 and are never read) --
+// a template parameter, so the plain Reduce's unrolled root loads carry no branch.
+template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false>
 __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   static_assert(!NV1 || (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4), "NV1 is a Reduce-op form");
+  static_assert(!ZR || (MODE == RM_REDUCE && OP != OP_REPLACE), "ZR is a Reduce-op form");
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;   // accumulator pack bytes
   constexpr int U = VB >= 16 ? 2 : 4;
@@ -870,7 +874,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
         mk[u] = 0;
         if (k < t.cnt) {
           mk[u] = (__ldg(mw + (k >> 5)) >> (k & 31)) & 1u;
-          if constexpr (need_root) x[u] = ld_root<T, VB>(rbase, k, MODE == RM_REDUCE && a.zero_root);
+          if constexpr (need_root) x[u] = ld_root<T, VB>(rbase, k, ZR);
           if constexpr (need_leaf) y[u] = ld<T, VB>(lbase, k);
         }
       }
@@ -919,7 +923,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (on[u]) {
-          if constexpr (SingleReads<OP, MODE>::root) x[u] = ld_root<T, VB>(a.root, ri[u], MODE == RM_REDUCE && a.zero_root);
+          if constexpr (SingleReads<OP, MODE>::root) x[u] = ld_root<T, VB>(a.root, ri[u], ZR);
           if constexpr (SingleReads<OP, MODE>::leaf) y[u] = ld<T, VB>(a.leaf, li[u]);
         }
 #pragma unroll
@@ -972,7 +976,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       if constexpr (NV1) {   // one vector per unit: gather-then-fold (the CTA agrees on the stage first)
         __shared__ alignas(16) unsigned char s_val[RM_FLAT_BYTES];
         if (__syncthreads_and(staged))
-          fold_tile_flat<T, VB, OP>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+          fold_tile_flat<T, VB, OP, ZR>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
         return;
       } else {
         if (!staged) return;
@@ -990,35 +994,35 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
             simple &= b[j].comb < 0;
           }
           if (simple) {
-            fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v, a.zero_root);
+            fold_many<T, VB, OP, NB, true>(a.root, a.leaf, s_leaf, l0, nv, b, v, ZR);
           } else {
   #pragma unroll
             for (int j = 0; j < NB; ++j)
               fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv, b[j],
-                                                v[j], a.zero_root);
+                                                v[j], ZR);
           }
         }
         for (; w < work; w += kThreads) {
           const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
           fold_block<T, VB, OP, MODE, true>(a.root, a.leaf, s_leaf, l0, a.combs, a.partial, a.counter, nv,
-                                            load_block(s_rec, a.combs, t.a + cl - r0), v, a.zero_root);
+                                            load_block(s_rec, a.combs, t.a + cl - r0), v, ZR);
         }
       }
     } else {
       for (int32_t w = threadIdx.x; w < work; w += kThreads) {
         const int32_t cl = nv == 1 ? w : div_by(w, a.nv_m, a.nv_s), v = w - cl * nv;
         fold_block<T, VB, OP, MODE>(a.root, a.leaf, a.m_leaf, 0, a.combs, a.partial, a.counter, nv,
-                                    load_block(a.blocks, a.combs, t.a + cl), v, a.zero_root);
+                                    load_block(a.blocks, a.combs, t.a + cl), v, ZR);
       }
     }
   }
 }
 
-template <typename T, int VB, int OP, int MODE, bool NV1 = false>
+template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false>
 __global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
     rm_kernel(RmArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
-  rm_tile<T, VB, OP, MODE, NV1>(a, t);
+  rm_tile<T, VB, OP, MODE, NV1, ZR>(a, t);
 }
 
 // ------------------------------------------------------------------ diagonal-chunk Reduce
@@ -1137,29 +1141,40 @@ __global__ void __launch_bounds__(kThreads, 4) dg_kernel(DgArgs a) {
 }
 
 // ------------------------------------------------------------------ staged diagonal-chunk Reduce
-// The same Reduce as dg_kernel, for one forest, with its tiles staged in shared memory by the
-// bulk-copy engine: a persistent CTA loops over the plan's tiles (DgTile: up to 64 chunks of one
-// delta) and keeps two stages, so the next tile's copies are in flight while it folds this one.
-// Per tile, thread 0 issues up to four cp.async.bulk copies on the stage's mbarrier -- the
-// roots (unless the Reduce starts from zero), the diagonal leaves (the span widened to 16-byte
-// boundaries inside the leaf array), the chunk records and the tile's x entries -- so every
-// byte the tile must read except the other leaves of two-leaf roots (a gather, 15% of the roots
-// of the SpMV scatter) arrives in one round.  A tile whose roots are all in the plan writes them
-// back with one bulk store; others store root by root.  Units outside a copied span (the ends of
-// the arrays) are read and written directly.  Base pointers must be 16-byte aligned.
+// The same Reduce as dg_kernel, for one forest, as a warp-specialised pipeline: a persistent CTA
+// per SM of one producer warp and DG_CONSUMERS consumer warps loops over the plan's tiles
+// (DgTile: up to 32 chunks of one delta) through DgStage<VB>::NSTAGE shared-memory stages.
+//  - The producer fills a stage with up to five cp.async.bulk copies on the stage's "full"
+//    mbarrier -- the roots (unless the Reduce starts from zero), the diagonal leaves (the span
+//    widened to 16-byte boundaries inside the leaf array), the chunk records, the x entries and
+//    the list entries -- and refills it once the consumers have released it on its "empty"
+//    mbarrier.  Its warp fetches tile descriptors 32 at a time, so issuing waits on nothing.
+//  - A consumer warp owns DGB_WARP_CHUNKS chunks of every tile.  Before folding tile k it issues,
+//    for tile k + 1 (already landed or landing), the cp.async gathers of its roots' other leaves
+//    into the stage (the only reads that depend on staged data), so their latency hides behind
+//    a whole tile of work; each thread later reads only the slots it gathered itself, so no
+//    CTA-wide barrier is needed.  The fold then runs from shared memory alone, and each warp
+//    stores its 32 consecutive roots per chunk with coalesced global stores.
+// Waits are bounded (DEVSTAT_STAGE_TIMEOUT); units outside a copied span (the ends of the
+// arrays) are read and written directly.  Base pointers must be 16-byte aligned.
 struct DgBulkArgs {
   DgArgs a;
   const DgTile *tiles;
   int32_t ntiles;
-  int32_t *status;        // forest status word (a bulk copy that did not land)
+  int32_t *status;        // forest status word (a wait that ran out)
   int64_t root_bytes;     // bytes of the root and leaf arrays (spans are clamped inside them)
   int64_t leaf_bytes;
 };
 
+constexpr int DG_CONSUMERS = 16;                                  // consumer warps of a CTA
+constexpr int DGB_WARP_CHUNKS = DG_TILE_CHUNKS / DG_CONSUMERS;    // chunks of a tile per consumer warp
+constexpr int DG_BULK_THREADS = (DG_CONSUMERS + 1) * 32;
+static_assert(DGB_WARP_CHUNKS * DG_CONSUMERS == DG_TILE_CHUNKS, "the consumers share a tile evenly");
+
 // Shared-memory stage of one tile of VB-byte units: roots, diagonal leaves, chunk records, x
-// entries, list entries, and the gathered leaf values of the lists.  Widening a span to 16-byte
-// boundaries adds less than 16 bytes at each end, so the leaf, x and list areas have 32 bytes to
-// spare.
+// entries, list entries, the gathered list leaf values and the gathered other leaves of
+// two-leaf roots (one slot per x entry).  Widening a span to 16-byte boundaries adds less than
+// 16 bytes at each end, so the leaf, x and list areas have 32 bytes to spare.
 template <int VB> struct DgStage {
   static constexpr int R = DG_TILE_CHUNKS * 32 * VB;
   static constexpr int O_LEAF = R;
@@ -1167,8 +1182,13 @@ template <int VB> struct DgStage {
   static constexpr int O_X = O_REC + DG_TILE_CHUNKS * 16;
   static constexpr int O_L = O_X + DG_TILE_XCAP * 4 + 32;
   static constexpr int O_LV = O_L + DG_TILE_LCAP * 4 + 32;
-  static constexpr int BYTES = (O_LV + DG_TILE_LCAP * VB + 127) / 128 * 128;
+  static constexpr int O_PV = O_LV + DG_TILE_LCAP * VB;
+  static constexpr int BYTES = (O_PV + DG_TILE_XCAP * VB + 127) / 128 * 128;
+  // as many stages as fit one CTA per SM (about 200 KB), at most 8: tiles in flight keep the
+  // loads of an SM deep enough to cover DRAM latency
+  static constexpr int NSTAGE = (200 * 1024) / BYTES < 8 ? (200 * 1024) / BYTES : 8;
 };
+constexpr int DG_MAX_STAGES = 8;
 
 // One bulk copy global -> shared on mbarrier `bar` (sizes multiples of 16, both addresses
 // 16-byte aligned); the copy is counted in the barrier's expected bytes by the caller.
@@ -1177,14 +1197,32 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// The spans a tile stages (bytes, relative to each array's base).
+// Wait for phase `parity` of mbarrier `bar`, the thread suspended between tries (no spinning),
+// at most `limit` clock cycles; false if it did not complete.
+__device__ __forceinline__ bool mbar_sleep_wait(uint32_t bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity), "r"(1000000u) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// The spans a tile stages (bytes, relative to each array's base), computed once per tile by the
+// producer and kept in the stage's header for the consumers.
 struct DgSpans {
   int64_t u0, L0;          // first root unit, its diagonal leaf unit
-  int32_t n;               // roots of the tile (below the forest's last root)
-  int32_t rstage;          // root bytes staged (and stored back whole), a multiple of 16
   int64_t llo, lhi;        // leaf bytes [llo, lhi) staged
-  int64_t xlo, xhi;        // x-entry bytes [xlo, xhi) staged
-  int64_t lslo, lshi;      // list-entry bytes [lslo, lshi) staged (empty: lists read from global)
+  int64_t xlo, lslo;       // first staged x-entry and list-entry bytes
+  int32_t n;               // roots of the tile (below the forest's last root)
+  int32_t rstage;          // root bytes staged, a multiple of 16
+  int32_t xb, sb;          // staged x-entry and list-entry bytes (sb 0: lists read from global)
+  int32_t lofs;            // stage offset of diagonal leaf 0 (fast tiles)
+  int32_t fast;            // roots and diagonal leaves staged whole
+  int32_t c, tn, xbeg, lbeg, full, pad;   // the tile's fields
 };
 template <int VB>
 __device__ __forceinline__ DgSpans dg_spans(const DgBulkArgs &b, const DgTile &t) {
@@ -1198,200 +1236,239 @@ __device__ __forceinline__ DgSpans dg_spans(const DgBulkArgs &b, const DgTile &t
   p.lhi = min(((p.L0 + p.n) * VB + 15) & ~int64_t(15), b.leaf_bytes & ~int64_t(15));
   if (p.lhi < p.llo) p.lhi = p.llo;
   p.xlo = (int64_t(t.xbeg) * 4) & ~int64_t(15);
-  p.xhi = (int64_t(t.xend) * 4 + 15) & ~int64_t(15);
-  if (t.xend == t.xbeg) p.xhi = p.xlo;
+  p.xb = t.xend == t.xbeg ? 0 : int32_t(((int64_t(t.xend) * 4 + 15) & ~int64_t(15)) - p.xlo);
   p.lslo = (int64_t(t.lbeg) * 4) & ~int64_t(15);
-  p.lshi = (int64_t(t.lend) * 4 + 15) & ~int64_t(15);
-  if (t.lend == t.lbeg || t.lend - t.lbeg > DG_TILE_LCAP) p.lshi = p.lslo;
+  p.sb = t.lend == t.lbeg || t.lend - t.lbeg > DG_TILE_LCAP
+             ? 0 : int32_t(((int64_t(t.lend) * 4 + 15) & ~int64_t(15)) - p.lslo);
+  p.lofs = int32_t(DgStage<VB>::O_LEAF + (p.L0 * VB - p.llo));
+  p.fast = p.rstage == p.n * VB && p.llo <= p.L0 * VB && p.lhi >= (p.L0 + p.n) * VB;
+  p.c = t.c;
+  p.tn = t.n;
+  p.xbeg = t.xbeg;
+  p.lbeg = t.lbeg;
+  p.full = t.full;
+  p.pad = 0;
   return p;
 }
 
-template <typename T, int VB>
-__device__ __forceinline__ void dg_issue(const DgBulkArgs &b, unsigned char *sg, uint32_t bar, int32_t t) {
+// Producer: the stage's header, then up to five bulk copies on its "full" mbarrier.
+template <int VB>
+__device__ __forceinline__ void dg_issue(const DgBulkArgs &b, unsigned char *sg, DgSpans *hdr, uint32_t bar,
+                                         const DgTile &tl) {
   using S = DgStage<VB>;
-  const DgTile tl = b.tiles[t];
   const DgSpans p = dg_spans<VB>(b, tl);
+  *hdr = p;   // published to the consumers by the barrier's completion
   const uint32_t rb = b.a.zero_root ? 0u : uint32_t(p.rstage);
-  const uint32_t lb = uint32_t(p.lhi - p.llo), cb = uint32_t(tl.n) * 16u, xb = uint32_t(p.xhi - p.xlo);
-  const uint32_t sb = uint32_t(p.lshi - p.lslo);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(rb + lb + cb + xb + sb)
-               : "memory");
+  const uint32_t lb = uint32_t(p.lhi - p.llo), cb = uint32_t(tl.n) * 16u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(rb + lb + cb + uint32_t(p.xb) + uint32_t(p.sb)) : "memory");
   if (rb) bulk_load(sg, static_cast<const char *>(b.a.root) + p.u0 * VB, rb, bar);
   if (lb) bulk_load(sg + S::O_LEAF, static_cast<const char *>(b.a.leaf) + p.llo, lb, bar);
   bulk_load(sg + S::O_REC, b.a.chunks + tl.c, cb, bar);
-  if (xb) bulk_load(sg + S::O_X, reinterpret_cast<const char *>(b.a.x) + p.xlo, xb, bar);
-  if (sb) bulk_load(sg + S::O_L, reinterpret_cast<const char *>(b.a.lists) + p.lslo, sb, bar);
+  if (p.xb) bulk_load(sg + S::O_X, reinterpret_cast<const char *>(b.a.x) + p.xlo, uint32_t(p.xb), bar);
+  if (p.sb) bulk_load(sg + S::O_L, reinterpret_cast<const char *>(b.a.lists) + p.lslo, uint32_t(p.sb), bar);
 }
 
-// Fold one staged tile; the results of a full tile go back into the stage's root area.  FAST:
-// the tile's roots and diagonal leaves are staged whole (no array end inside the tile), so
-// every root and diagonal leaf is read from shared memory at a fixed offset, in 32 bits.
+// What a consumer lane keeps of a tile between its gathers and its fold: per chunk the root's
+// code and its x entry's index relative to the tile (or -1).
+struct DgLane {
+  uint32_t code[DGB_WARP_CHUNKS];
+  int32_t xi[DGB_WARP_CHUNKS];
+};
+
+// A consumer's gathers for a landed tile: for each of its chunks, the other leaf of every
+// two-leaf root into its x entry's slot, and the list leaves of every list root into theirs
+// (staged lists only), by cp.async; then one commit group.
+template <int VB>
+__device__ __forceinline__ DgLane dg_gather(const DgBulkArgs &b, unsigned char *sg, const DgSpans p) {
+  using S = DgStage<VB>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t below = (1u << lane) - 1u;
+  const int32_t *xs = reinterpret_cast<const int32_t *>(sg + S::O_X) + (p.xbeg - int32_t(p.xlo / 4));   // by tile index
+  const int32_t *sl = reinterpret_cast<const int32_t *>(sg + S::O_L) - int32_t(p.lslo / 4);
+  const char *leaf = static_cast<const char *>(b.a.leaf);
+  DgLane d;
+#pragma unroll
+  for (int j = 0; j < DGB_WARP_CHUNKS; ++j) {
+    const int32_t cc = warp * DGB_WARP_CHUNKS + j;
+    d.code[j] = DG_SKIP;
+    d.xi[j] = -1;
+    if (cc >= p.tn) continue;
+    const uint4 rec = *reinterpret_cast<const uint4 *>(sg + S::O_REC + cc * 16);
+    const uint32_t code = ((lane >= 16 ? rec.y : rec.x) >> (2 * (lane & 15))) & 3u;
+    const uint32_t more = __ballot_sync(0xffffffffu, code >= DG_PAIR);
+    const int32_t xi = int32_t(rec.z) - p.xbeg + __popc(more & below);
+    d.code[j] = code;
+    if (code == DG_PAIR) {
+      d.xi[j] = xi;
+      cp_async_vec<VB>(sg + S::O_PV + xi * VB, leaf + int64_t(xs[xi] & 0x7fffffff) * VB);
+    } else if (code == DG_LIST) {
+      d.xi[j] = xi;
+      if (p.sb) {
+        const int32_t o = xs[xi], h = -1 - sl[o], n = (h & 0xffff) + (h >> 16);
+        for (int32_t k = 1; k <= n; ++k)
+          cp_async_vec<VB>(sg + S::O_LV + (o + k - p.lbeg) * VB, leaf + int64_t(sl[o + k]) * VB);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  return d;
+}
+
+// A consumer's fold of its chunks of a staged tile (its gathers have landed); the results of a
+// full tile go back into the stage's root area, others straight to the root array.  FAST: the
+// tile's roots and diagonal leaves are staged whole, so both are read at fixed offsets.
 template <typename T, int VB, int OP, bool FAST>
-__device__ __forceinline__ void dg_fold_stage(const DgBulkArgs &b, unsigned char *sg, const DgTile &tl,
-                                              const DgSpans &p) {
+__device__ __forceinline__ void dg_fold_stage(const DgBulkArgs &b, unsigned char *sg, const DgSpans p,
+                                              const DgLane &d) {
   using A = typename Acc<T, OP>::type;
   using S = DgStage<VB>;
   using P = Pack<T, VB>;
   const DgArgs &a = b.a;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t below = (1u << lane) - 1u;
-  const int sh = 2 * (lane & 15);
-  const bool hi = lane >= 16;
-  const int32_t *xs = reinterpret_cast<const int32_t *>(sg + S::O_X) - p.xlo / 4;   // xs[e]: x entry e
-  const bool zr = a.zero_root, whole = tl.full;
-  const uint32_t lofs = FAST ? uint32_t(S::O_LEAF + (p.L0 * VB - p.llo)) : 0u;   // diagonal leaf 0 in the stage
-  auto root_ld = [&](int32_t i) -> P {
+  const int32_t *xs = reinterpret_cast<const int32_t *>(sg + S::O_X) + (p.xbeg - int32_t(p.xlo / 4));
+  const int32_t *sl = reinterpret_cast<const int32_t *>(sg + S::O_L) - int32_t(p.lslo / 4);
+  const bool zr = a.zero_root;
+#pragma unroll
+  for (int j = 0; j < DGB_WARP_CHUNKS; ++j) {
+    const uint32_t code = d.code[j];
+    if (code == DG_SKIP) continue;
+    const int32_t i = (warp * DGB_WARP_CHUNKS + j) * 32 + lane;
+    P xr, yd;
     if (FAST) {
-      if (zr) return ld_root<T, VB>(nullptr, 0, true);
-      return *reinterpret_cast<const P *>(sg + i * VB);
+      xr = zr ? ld_root<T, VB>(nullptr, 0, true) : *reinterpret_cast<const P *>(sg + i * VB);
+      yd = *reinterpret_cast<const P *>(sg + p.lofs + i * VB);
+    } else {
+      xr = !zr && i * VB < p.rstage ? *reinterpret_cast<const P *>(sg + i * VB) : ld_root<T, VB>(a.root, p.u0 + i, zr);
+      const int64_t gb = (p.L0 + i) * VB;
+      yd = gb >= p.llo && gb + VB <= p.lhi ? *reinterpret_cast<const P *>(sg + S::O_LEAF + (gb - p.llo))
+                                           : ld<T, VB>(a.leaf, p.L0 + i);
     }
-    if (!zr && i * VB < p.rstage) return *reinterpret_cast<const P *>(sg + i * VB);
-    return ld_root<T, VB>(a.root, p.u0 + i, zr);
-  };
-  auto leaf_ld = [&](int32_t i) -> P {
-    if (FAST) return *reinterpret_cast<const P *>(sg + lofs + uint32_t(i) * VB);
-    const int64_t gb = (p.L0 + i) * VB;
-    if (gb >= p.llo && gb + VB <= p.lhi) return *reinterpret_cast<const P *>(sg + S::O_LEAF + (gb - p.llo));
-    return ld<T, VB>(a.leaf, p.L0 + i);
-  };
-  auto root_st = [&](int32_t i, const P &r) {
-    if (FAST ? whole : whole && i * VB < p.rstage) *reinterpret_cast<P *>(sg + i * VB) = r;
-    else st<T, VB>(a.root, p.u0 + i, r);
-  };
-  // the leaf values of the tile's lists (staged list entries >= 0; headers are negative),
-  // gathered by the whole CTA into shared memory with cp.async, awaited before the fold
-  const bool lstaged = p.lshi > p.lslo;
-  const int32_t *sl = reinterpret_cast<const int32_t *>(sg + S::O_L) - p.lslo / 4;   // sl[o]: list entry o
-  P *slv = reinterpret_cast<P *>(sg + S::O_LV) - tl.lbeg;                             // slv[o]: its leaf value
-  if (lstaged)
-    for (int32_t o = tl.lbeg + int32_t(threadIdx.x); o < tl.lend; o += kThreads) {
-      const int32_t e = sl[o];
-      if (e >= 0) cp_async_vec<VB>(slv + o, static_cast<const char *>(a.leaf) + int64_t(e) * VB);
-    }
-  constexpr int J = DG_WARP_CHUNKS;
-  uint32_t code[J];
-  int32_t xe[J];
-  P xr[J], yd[J], yo[J];
+    Pack<A, int(sizeof(A)) * P::L> acc;
+    if (code == DG_DIAG) {
 #pragma unroll
-  for (int j = 0; j < J; ++j) {   // staged values, and the gathers of the other leaves
-    const int32_t cc = warp * J + j, i = cc * 32 + lane;
-    code[j] = 0;
-    xe[j] = 0;
-    if (cc < tl.n) {
-      const uint4 rec = *reinterpret_cast<const uint4 *>(sg + S::O_REC + cc * 16);
-      code[j] = ((hi ? rec.y : rec.x) >> sh) & 3u;
-      const uint32_t more = __ballot_sync(0xffffffffu, code[j] >= DG_PAIR);
-      if (code[j] >= DG_PAIR) xe[j] = xs[int32_t(rec.z) + __popc(more & below)];
-      if (code[j] != DG_SKIP) {
-        xr[j] = root_ld(i);
-        yd[j] = leaf_ld(i);
-      }
-      if (code[j] == DG_PAIR) yo[j] = ld<T, VB>(a.leaf, xe[j] & 0x7fffffff);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
+      for (int l = 0; l < P::L; ++l) acc.v[l] = to_acc<A, T>(yd.v[l]);
+    } else if (code == DG_PAIR) {
+      // canonical order: the other leaf first unless its entry has the top bit (after)
+      const bool after = xs[d.xi[j]] < 0;
+      const P yo = *reinterpret_cast<const P *>(sg + S::O_PV + d.xi[j] * VB);
+      const P &y0 = after ? yd : yo, &y1 = after ? yo : yd;
 #pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int32_t i = (warp * J + j) * 32 + lane;
-    if (code[j] == DG_DIAG || code[j] == DG_PAIR) {
-      const bool pair = code[j] == DG_PAIR, after = xe[j] < 0;
-      const P &y0 = pair && !after ? yo[j] : yd[j];
-      P r = xr[j];
-#pragma unroll
-      for (int l = 0; l < P::L; ++l) {
-        A acc = to_acc<A, T>(y0.v[l]);
-        if (pair) acc = combine<OP, A>(acc, to_acc<A, T>(after ? yo[j].v[l] : yd[j].v[l]));
-        r.v[l] = apply_acc<OP, T, A>(xr[j].v[l], acc);
-      }
-      root_st(i, r);
-    } else if (code[j] == DG_LIST) {
+      for (int l = 0; l < P::L; ++l) acc.v[l] = combine<OP, A>(to_acc<A, T>(y0.v[l]), to_acc<A, T>(y1.v[l]));
+    } else {
       // three or more leaves: the list (header, then the other leaves) and its gathered values
       // in shared memory, or from global memory for a tile whose lists did not fit the stage
-      const int32_t o = xe[j], h = -1 - (lstaged ? sl[o] : __ldg(a.lists + o));
+      const int32_t o = xs[d.xi[j]], h = -1 - (p.sb ? sl[o] : __ldg(a.lists + o));
       const int32_t nb = h & 0xffff, nl = nb + 1 + (h >> 16);
-      Pack<A, int(sizeof(A)) * P::L> acc;
       for (int32_t k = 0; k < nl; ++k) {
         const int32_t ok = o + 1 + (k < nb ? k : k - 1);
-        const P y = k == nb ? yd[j] : lstaged ? slv[ok] : ld<T, VB>(a.leaf, __ldg(a.lists + ok));
+        const P y = k == nb ? yd
+                            : p.sb ? *reinterpret_cast<const P *>(sg + S::O_LV + (ok - p.lbeg) * VB)
+                                   : ld<T, VB>(a.leaf, __ldg(a.lists + ok));
 #pragma unroll
         for (int l = 0; l < P::L; ++l)
           acc.v[l] = k == 0 ? to_acc<A, T>(y.v[l]) : combine<OP, A>(acc.v[l], to_acc<A, T>(y.v[l]));
       }
-      P r = xr[j];
-#pragma unroll
-      for (int l = 0; l < P::L; ++l) r.v[l] = apply_acc<OP, T, A>(xr[j].v[l], acc.v[l]);
-      root_st(i, r);
     }
+    P r;
+#pragma unroll
+    for (int l = 0; l < P::L; ++l) r.v[l] = apply_acc<OP, T, A>(xr.v[l], acc.v[l]);
+    st<T, VB>(a.root, p.u0 + i, r);   // coalesced: a warp's lanes hold consecutive roots
   }
 }
 
 // A tile at an end of the root or leaf array (rare): out of line, so that the common path keeps
 // its registers.
 template <typename T, int VB, int OP>
-__device__ __noinline__ void dg_fold_edge(const DgBulkArgs &b, unsigned char *sg, const DgTile &tl, const DgSpans &p) {
-  dg_fold_stage<T, VB, OP, false>(b, sg, tl, p);
+__device__ __noinline__ void dg_fold_edge(const DgBulkArgs &b, unsigned char *sg, const DgSpans &p, const DgLane &d) {
+  dg_fold_stage<T, VB, OP, false>(b, sg, p, d);
 }
 
-// Four CTAs per SM for units up to 8 bytes (two stages of 27 KB for 8-byte units, 64 registers);
-// 16-byte units fit two.
 template <typename T, int VB, int OP>
-__global__ void __launch_bounds__(kThreads, VB >= 16 ? 2 : 3) dg_bulk_kernel(DgBulkArgs b) {
+__global__ void __launch_bounds__(DG_BULK_THREADS, 1) dg_bulk_kernel(DgBulkArgs b) {
   using S = DgStage<VB>;
+  constexpr int DG_STAGES = S::NSTAGE;
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ alignas(8) uint64_t bar[2];
-  const uint32_t b0 = smem_addr(&bar[0]), b1 = smem_addr(&bar[1]);
+  __shared__ alignas(8) uint64_t full[DG_MAX_STAGES], empty[DG_MAX_STAGES];
+  __shared__ DgSpans hdr[DG_MAX_STAGES];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1) : "memory");
+    for (int s = 0; s < DG_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])), "r"(DG_CONSUMERS) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const int32_t G = gridDim.x;
-  if (threadIdx.x == 0) {
-    if (int32_t(blockIdx.x) < b.ntiles) dg_issue<T, VB>(b, dsm, b0, blockIdx.x);
-    if (int32_t(blockIdx.x) + G < b.ntiles) dg_issue<T, VB>(b, dsm + S::BYTES, b1, blockIdx.x + G);
+  const int32_t nk = b.ntiles > int32_t(blockIdx.x) ? (b.ntiles - int32_t(blockIdx.x) + G - 1) / G : 0;   // tiles of this CTA
+  if (warp == DG_CONSUMERS) {
+    // producer: fill stage k % S with tile k once its previous tile (k - S) is folded.  The warp
+    // fetches the descriptors of 32 tiles at a time, one per lane, and lane 0 takes each by
+    // shuffle, so no issue waits on a descriptor load.
+    int4 d0 = make_int4(0, 0, 0, 0), d1 = d0;
+    bool stop = false;
+    for (int32_t k = 0; k < nk; ++k) {
+      if ((k & 31) == 0 && k + lane < nk) {
+        const int4 *src = reinterpret_cast<const int4 *>(b.tiles + blockIdx.x + (k + lane) * G);
+        d0 = __ldg(src);
+        d1 = __ldg(src + 1);
+      }
+      const int src_lane = k & 31;
+      DgTile tl;
+      tl.c = __shfl_sync(0xffffffffu, d0.x, src_lane);
+      tl.n = __shfl_sync(0xffffffffu, d0.y, src_lane);
+      tl.delta = __shfl_sync(0xffffffffu, d0.z, src_lane);
+      tl.xbeg = __shfl_sync(0xffffffffu, d0.w, src_lane);
+      tl.xend = __shfl_sync(0xffffffffu, d1.x, src_lane);
+      tl.full = __shfl_sync(0xffffffffu, d1.y, src_lane);
+      tl.lbeg = __shfl_sync(0xffffffffu, d1.z, src_lane);
+      tl.lend = __shfl_sync(0xffffffffu, d1.w, src_lane);
+      const int s = k % DG_STAGES;
+      if (lane == 0) {
+        if (k >= DG_STAGES &&
+            !mbar_sleep_wait(smem_addr(&empty[s]), uint32_t((k - DG_STAGES) / DG_STAGES) & 1u, kWaitCycles)) {
+          // the consumers stopped: record it, let the loads still in flight land (bounded), stop
+          if (b.status) atomicOr(b.status, DEVSTAT_STAGE_TIMEOUT);
+          for (int32_t kk = k - DG_STAGES; kk < k; ++kk)
+            mbar_sleep_wait(smem_addr(&full[kk % DG_STAGES]), uint32_t(kk / DG_STAGES) & 1u, kWaitCycles);
+          stop = true;
+        } else {
+          dg_issue<VB>(b, dsm + s * S::BYTES, &hdr[s], smem_addr(&full[s]), tl);
+        }
+      }
+      if (__shfl_sync(0xffffffffu, int(stop), 0)) break;
+    }
+    return;
   }
-  uint32_t phase = 0;   // bit s: the parity stage s waits for next
-  int32_t i = 0;
-  for (int32_t t = blockIdx.x; t < b.ntiles; t += G, ++i) {
-    const int s = i & 1;
+  // consumers: gathers of tile k + 1 before the fold of tile k
+  auto landed = [&](int32_t k) {
+    return mbar_sleep_wait(smem_addr(&full[k % DG_STAGES]), uint32_t(k / DG_STAGES) & 1u, kWaitCycles);
+  };
+  bool ok = nk == 0 || landed(0);
+  DgLane cur{};
+  if (ok && nk > 0) cur = dg_gather<VB>(b, dsm, hdr[0]);
+  for (int32_t k = 0; ok && k < nk; ++k) {
+    const int s = k % DG_STAGES;
     unsigned char *sg = dsm + s * S::BYTES;
-    const uint32_t bs = s ? b1 : b0;
-    const bool ok = mbar_wait(bs, (phase >> s) & 1u, kWaitCycles);
-    if (!__syncthreads_and(ok)) {
-      // a copy did not land: record it, let this tile's and the other stage's copies finish
-      // (bounded), wait for the stores, and stop
-      if (threadIdx.x == 0) {
-        if (b.status) atomicOr(b.status, DEVSTAT_STAGE_TIMEOUT);
-        mbar_wait(bs, (phase >> s) & 1u, kWaitCycles);
-        if (t + G < b.ntiles) mbar_wait(s ? b0 : b1, (phase >> (s ^ 1)) & 1u, kWaitCycles);
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-      }
-      return;
+    DgLane nxt{};
+    if (k + 1 < nk) {
+      if (!(ok = landed(k + 1))) break;
+      const int sn = (k + 1) % DG_STAGES;
+      nxt = dg_gather<VB>(b, dsm + sn * S::BYTES, hdr[sn]);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // tile k's gathers
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    phase ^= 1u << s;
-    const DgTile tl = b.tiles[t];
-    const DgSpans p = dg_spans<VB>(b, tl);
-    if (p.rstage == p.n * VB && p.llo <= p.L0 * VB && p.lhi >= (p.L0 + p.n) * VB)
-      dg_fold_stage<T, VB, OP, true>(b, sg, tl, p);
-    else
-      dg_fold_edge<T, VB, OP>(b, sg, tl, p);
-    // the folded roots of a full tile leave by one bulk store; then the stage takes tile t + 2G
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (tl.full && p.rstage > 0) {
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                     ::"l"(static_cast<char *>(b.a.root) + p.u0 * VB), "r"(smem_addr(sg)), "r"(uint32_t(p.rstage))
-                     : "memory");
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      }
-      if (t + 2 * G < b.ntiles) dg_issue<T, VB>(b, sg, bs, t + 2 * G);
-    }
+    const DgSpans p = hdr[s];   // read once: the header lives in shared memory
+    if (p.fast) dg_fold_stage<T, VB, OP, true>(b, sg, p, cur);
+    else dg_fold_edge<T, VB, OP>(b, sg, p, cur);
+    cur = nxt;
+    __syncwarp();   // every lane is done with the stage: release it
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[s])) : "memory");
   }
-  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (!ok && lane == 0 && b.status) atomicOr(b.status, DEVSTAT_STAGE_TIMEOUT);
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ roots without leaves

@@ -15,13 +15,18 @@ cudaError_t go_ts(const TsLaunch &L) {
 template <typename T, int VB, int OP, int MODE>
 cudaError_t go_rm(const RmLaunch &L) {
   if (L.ntiles <= 0) return cudaSuccess;
+  // A single forest's Reduce from zero runs the ZR instantiation; REPLACE reads no root, and
+  // the batch tables never start roots at zero.
+  constexpr bool kZr = MODE == RM_REDUCE && OP != OP_REPLACE;
+  const bool zr = kZr && !L.tiles && L.single->zero_root;
   if (L.nv1) {   // the one-vector-unit kernel; the caller passed tiles of rm_fold_nv1_tiles
     if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
       if (L.tiles) {
         rm_batch_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
       } else {
         if (L.single->nv != 1) return cudaErrorInvalidValue;
-        rm_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+        if (zr) rm_kernel<T, VB, OP, MODE, true, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+        else rm_kernel<T, VB, OP, MODE, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
       }
       return cudaGetLastError();
     } else {
@@ -31,6 +36,12 @@ cudaError_t go_rm(const RmLaunch &L) {
   if (L.tiles) {
     rm_batch_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
     return cudaGetLastError();
+  }
+  if constexpr (kZr) {
+    if (zr) {
+      rm_kernel<T, VB, OP, MODE, false, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
+      return cudaGetLastError();
+    }
   }
   rm_kernel<T, VB, OP, MODE><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
   return cudaGetLastError();
@@ -106,17 +117,18 @@ cudaError_t go_dg(const DgLaunch &L) {
   return cudaGetLastError();
 }
 
-// The staged kernel: a persistent grid of as many CTAs as fit the GPU (two stages of
+// The staged kernel: a persistent grid of as many CTAs as fit the GPU (DG_STAGES stages of
 // DgStage<VB> in dynamic shared memory each).  cudaErrorNotSupported when it cannot be set up.
 template <typename T, int VB, int OP>
 cudaError_t go_dg_bulk(const DgBulkArgs &b, cudaStream_t s) {
   if (b.ntiles <= 0) return cudaSuccess;
-  constexpr int smem = 2 * DgStage<VB>::BYTES;
+  constexpr int smem = DgStage<VB>::NSTAGE * DgStage<VB>::BYTES;
   static const int per_sm = [] {
     int n = 0;
     if (cudaFuncSetAttribute(dg_bulk_kernel<T, VB, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dg_bulk_kernel<T, VB, OP>, kThreads, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dg_bulk_kernel<T, VB, OP>, DG_BULK_THREADS, smem) !=
+            cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -129,7 +141,7 @@ cudaError_t go_dg_bulk(const DgBulkArgs &b, cudaStream_t s) {
     return cudaErrorNotSupported;
   }
   const int grid = b.ntiles < per_sm * sms ? b.ntiles : per_sm * sms;
-  dg_bulk_kernel<T, VB, OP><<<grid, kThreads, smem, s>>>(b);
+  dg_bulk_kernel<T, VB, OP><<<grid, DG_BULK_THREADS, smem, s>>>(b);
   return cudaGetLastError();
 }
 

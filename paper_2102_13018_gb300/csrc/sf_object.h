@@ -61,6 +61,13 @@ struct sf_s {
   int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
   int32_t tuned_mode = SF_MODE_DETERMINISTIC;   // what AUTO means (sf_autotune may change it)
   int32_t tuned_path = SF_PATH_FUSED;
+  int32_t plan = SF_PLAN_AUTO;       // deterministic Reduce plan (SF_PLAN_*)
+  int32_t tuned_plan = SF_PLAN_ROOT_MAJOR;   // what SF_PLAN_AUTO means (sf_autotune may change it)
+  int32_t vec_bytes = 0;             // widest vector of the Bcast / Reduce kernels (0: 16 bytes)
+  int32_t tile_edges = 0;            // edges per two-sided tile (0: the setup pass's choice)
+  sfgb::DevBuf ts_tuned;             // the two-sided tile list cut at tile_edges
+  const sfgb::TsTile *ts_default = nullptr;
+  int32_t n_ts_default = 0;
   std::vector<sfgb::Pending> pending;
   sf_t *multi = nullptr;             // multi-forest, built on first use (Gather / Scatter)
 };
@@ -71,7 +78,11 @@ std::atomic<int64_t> &launch_counter();
 int cuda_err(cudaError_t e);
 int ensure(DevBuf &b, size_t bytes, bool zero, cudaStream_t s);
 void release(DevBuf &b);
-int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs);
+int pick_vb(int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs, int cap = 16);
+// pick_vb under the forest's vector-width setting (sf_set_vector_bytes)
+inline int pick_vb_sf(const sf_t *sf, int w, int ub, bool allow_wide, std::initializer_list<const void *> ptrs) {
+  return pick_vb(w, ub, allow_wide, ptrs, sf->vec_bytes > 0 ? sf->vec_bytes : 16);
+}
 int check_unit(const sf_unit &u, int32_t op);
 int check_ptr(const void *p, int w);
 int launched(cudaError_t e);
@@ -80,10 +91,16 @@ TsArgs ts_args(const sf_t *sf, const TsTile *tiles, int32_t ntiles, const void *
 RmArgs rm_args(sf_t *sf, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd, int nv);
 RmArgs rm_args_plan(sf_t *sf, const DevPlan &d, const RmTile *tiles, int32_t ntiles, void *root, void *leaf, void *upd,
                     int nv);
+// SF_PLAN_ROOT_MAJOR, SF_PLAN_DIAGONAL or SF_PLAN_DIAGONAL_STAGED after resolving AUTO; a forest
+// without diagonal chunks always answers SF_PLAN_ROOT_MAJOR.
+inline int32_t reduce_plan(const sf_t *sf) {
+  if (sf->dp.dg_nchunks == 0) return SF_PLAN_ROOT_MAJOR;
+  return sf->plan == SF_PLAN_AUTO ? sf->tuned_plan : sf->plan;
+}
 // Whether a deterministic Reduce with `op` and nv vectors per unit runs on the diagonal chunks
 // (then on the root-major plan of the rest).
 inline bool reduce_dg(const sf_t *sf, int32_t op, int nv) {
-  return op != SF_REPLACE && nv == 1 && sf->dp.dg_nchunks > 0;
+  return op != SF_REPLACE && nv == 1 && reduce_plan(sf) != SF_PLAN_ROOT_MAJOR;
 }
 DgArgs dg_args(const sf_t *sf, const void *leaf, void *root);
 // Enqueue the deterministic (root-major or diagonal-chunk) Reduce with its fold scratch.
@@ -94,8 +111,8 @@ int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC af
 // Whether Reduce with `op` on `dtype` runs on the atomic two-sided kernels: in atomic mode
 // (floating SUM rounds in arrival order there), and in deterministic mode for operations whose
 // result does not depend on the order (integer SUM/MIN/MAX) while no root has more than
-// kOrderFreeMaxDegree leaves (same-address atomics serialise) and the forest has no diagonal
-// chunks.
+// kOrderFreeMaxDegree leaves (same-address atomics serialise) and the Reduce does not run on
+// the diagonal chunks.
 constexpr int64_t kOrderFreeMaxDegree = 1024;
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op);
 int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO

@@ -174,10 +174,10 @@ static_assert(sizeof(DiagChunk) == 16, "one 16-byte load per chunk");
 // A tile of the staged diagonal-chunk kernel: chunks [c, c + n) of the plan (n <= DG_TILE_CHUNKS),
 // one delta, x entries [xbeg, xend) (at most DG_TILE_XCAP), list entries [lbeg, lend) (at most
 // DG_TILE_LCAP), and whether every root of the tile (below the forest's last root) is in the
-// plan, so the tile may write its roots back whole.
+// plan.
 constexpr int32_t DG_TILE_CHUNKS = 32;
-constexpr int32_t DG_TILE_XCAP = DG_TILE_CHUNKS * 32;   // one x entry per root at most: never binding
-constexpr int32_t DG_TILE_LCAP = 512;
+constexpr int32_t DG_TILE_XCAP = 512;   // the SpMV scatter's tiles hold about 154 on average
+constexpr int32_t DG_TILE_LCAP = 256;   // and about 6 list roots
 struct DgTile {
   int32_t c, n, delta, xbeg, xend, full, lbeg, lend;
 };

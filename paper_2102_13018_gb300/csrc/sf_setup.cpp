@@ -227,6 +227,15 @@ void push_ts_tiles(std::vector<TsTile> &out, const Run &r, int64_t per) {
   }
 }
 
+}  // namespace
+
+void cut_ts_tiles(const HostPlan &plan, int32_t per, std::vector<TsTile> &out) {
+  out.clear();
+  for (const Run &r : plan.runs) push_ts_tiles(out, r, per);
+}
+
+namespace {
+
 // Smallest power of two in [lo, hi] that splits `work` into at most TILE_TARGET tiles (hi if
 // none does).
 int32_t tile_size(int64_t work, int32_t lo, int32_t hi) {

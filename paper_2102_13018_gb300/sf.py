@@ -12,12 +12,14 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _abi
-from ._abi import check, sf_info, sf_node, sf_unit
+from ._abi import check, sf_info, sf_node, sf_tuning, sf_unit
 
 OPS = {"REPLACE": _abi.SF_REPLACE, "SUM": _abi.SF_SUM, "MIN": _abi.SF_MIN, "MAX": _abi.SF_MAX}
 MODES = {"auto": _abi.SF_MODE_AUTO, "atomic": _abi.SF_MODE_ATOMIC, "deterministic": _abi.SF_MODE_DETERMINISTIC}
 PATHS = {"auto": _abi.SF_PATH_AUTO, "fused": _abi.SF_PATH_FUSED, "three_phase": _abi.SF_PATH_THREE_PHASE,
          "root_major": _abi.SF_PATH_ROOT_MAJOR}
+PLANS = {"auto": _abi.SF_PLAN_AUTO, "root_major": _abi.SF_PLAN_ROOT_MAJOR, "diagonal": _abi.SF_PLAN_DIAGONAL,
+         "diagonal_staged": _abi.SF_PLAN_DIAGONAL_STAGED}
 DTYPE_NAMES = {"int32": _abi.SF_INT32, "int64": _abi.SF_INT64, "fp32": _abi.SF_FP32, "fp64": _abi.SF_FP64,
                "bf16": _abi.SF_BF16}
 
@@ -154,6 +156,31 @@ class StarForest:
     def set_path(self, path: str) -> "StarForest":
         check(self._lib.sf_set_path(self._h, PATHS[path]), "sf_set_path")
         return self
+
+    def set_reduce_plan(self, plan: str) -> "StarForest":
+        """Plan of the deterministic Reduce: "auto", "root_major", "diagonal", "diagonal_staged"."""
+        check(self._lib.sf_set_reduce_plan(self._h, PLANS[plan]), "sf_set_reduce_plan")
+        return self
+
+    def set_vector_bytes(self, nbytes: int) -> "StarForest":
+        """Widest vector the kernels move per access (2, 4, 8, 16; 0 = 16)."""
+        check(self._lib.sf_set_vector_bytes(self._h, int(nbytes)), "sf_set_vector_bytes")
+        return self
+
+    def set_tile_edges(self, edges: int) -> "StarForest":
+        """Edges per CTA tile of the two-sided kernels (a power of two; 0 = the setup's)."""
+        check(self._lib.sf_set_tile_edges(self._h, int(edges)), "sf_set_tile_edges")
+        return self
+
+    def tuning(self) -> dict:
+        """The forest's current choices: Bcast path, Reduce mode and plan, vector bytes, tile edges."""
+        t = sf_tuning()
+        check(self._lib.sf_get_tuning(self._h, ctypes.byref(t)), "sf_get_tuning")
+        paths = {v: n for n, v in PATHS.items()}
+        modes = {v: n for n, v in MODES.items()}
+        plans = {v: n for n, v in PLANS.items()}
+        return {"path": paths[t.path], "mode": modes[t.mode], "vector_bytes": t.vector_bytes,
+                "tile_edges": t.tile_edges, "reduce_plan": plans[t.reduce_plan]}
 
     def destroy(self):
         if getattr(self, "_h", None) and getattr(self, "_owned", True):
@@ -363,8 +390,11 @@ class StarForest:
 
     # ---------------------------------------------------------------- autotuner
     def autotune(self, kind: str, src, dst, op: str, bs=None, reps: int = 3, stream=None) -> str:
-        """Time the Bcast data paths (kind "bcast") or Reduce modes (kind "reduce") and make
-        the fastest what "auto" means for this forest.  src/dst are not modified."""
+        """Time the Bcast variants (kind "bcast": path x vector width x tile size) or the Reduce
+        variants (kind "reduce": mode x vector width, the plan of the deterministic mode, tile size
+        for atomics) and keep the fastest; its path or mode becomes what "auto" means for this
+        forest (tuning() has the rest, the tuned plan becomes what reduce plan "auto" means).
+        src/dst are not modified."""
         root = src if kind == "bcast" else dst
         u = self._unit(root, self.nroots_total, bs)
         k = _abi.SF_OP_BCAST if kind == "bcast" else _abi.SF_OP_REDUCE

@@ -162,3 +162,73 @@ def test_batch_rebuilds_after_a_forest_scratch_grows():
         torch.cuda.synchronize()
         assert_bits_equal(to_host(r, "fp32"), want, f"batch run after the scratch moved (graph={use_graph})")
     assert sf.device_status() == 0
+
+
+@pytest.mark.parametrize("edges", [64, 512, 4096, 0])
+@pytest.mark.parametrize("vec", [4, 0])
+def test_tile_edges_and_vector_bytes_keep_results(edges, vec):
+    """The launch-shape knobs the tuner turns change no result: Bcast and the deterministic and
+    atomic Reduce against the oracle for every tile size and vector cap."""
+    f = sfgen.zipf_forest(33, 3, 20000, 6000, 4)
+    sf = StarForest.from_forest(f).setup().set_tile_edges(edges).set_vector_bytes(vec)
+    t = sf.tuning()
+    assert t["vector_bytes"] == vec and t["tile_edges"] == (edges or sf.info()["ts_tile_edges"])
+    for dtype, bs in (("fp64", 2), ("fp32", 8), ("int64", 3)):
+        root, leaf = make_data(f, dtype, bs, 1220)
+        for op in ("REPLACE", "SUM", "MAX"):
+            l = to_dev(leaf, dtype)
+            sf.bcast(to_dev(root, dtype), l, op, bs=bs)
+            assert_bits_equal(to_host(l, dtype), oracle.bcast(f, dtype, bs, root, leaf, op), f"bcast {op} {edges} {vec}")
+            want = oracle.reduce(f, dtype, bs, leaf, root, op)
+            for mode in ("deterministic", "atomic"):
+                r = to_dev(root, dtype)
+                sf.set_mode(mode).reduce(to_dev(leaf, dtype), r, op, bs=bs)
+                if mode == "atomic" and op == "SUM" and dtype.startswith("fp"):
+                    assert_atomic_sum_close(to_host(r, dtype), want, f, dtype, bs, leaf, root, "atomic")
+                else:
+                    assert_bits_equal(to_host(r, dtype), want, f"reduce {mode} {op} {edges} {vec}")
+    sf.set_mode("deterministic")
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_tuned_batch_matches_oracle_at_each_choice(use_graph):
+    """Every forest tuned on its own (path, mode, vector width, tile size), then run as one batch:
+    bit-exact where the tuner kept the deterministic Reduce, within the atomic bound where it
+    chose atomics.  Retuning one forest afterwards rebuilds the batch's tables."""
+    items = build(FORESTS[:16], modes=["auto"])
+    fresh(items)
+    choices = []
+    for it in items:
+        sf = it["sf"]
+        sf.autotune("bcast", it["r"], it["l"], it["op"], bs=it["bs"])
+        sf.autotune("reduce", it["l2"], it["r2"], it["op"], bs=it["bs"])
+        choices.append(sf.tuning())
+    assert all(c["path"] in ("fused", "root_major", "three_phase") for c in choices)
+    b = Batch().set_ops(ops_for(items))
+    for run in range(2):
+        fresh_inplace(items)
+        b.run(use_graph=use_graph)
+        torch.cuda.synchronize()
+        check_choices(items, choices)
+        if run == 0:      # retune one forest: its tile list and vector width change
+            items[0]["sf"].set_tile_edges(64).set_vector_bytes(2 if items[0]["dt"] == "bf16" else 0)
+            choices[0] = items[0]["sf"].tuning()
+
+
+def fresh_inplace(items):
+    for it in items:
+        for k, src in (("r", "root"), ("l", "leaf"), ("r2", "root"), ("l2", "leaf")):
+            it[k].copy_(to_dev(it[src], it["dt"]))
+
+
+def check_choices(items, choices):
+    for it, c in zip(items, choices):
+        f, dt, bs, op = it["f"], it["dt"], it["bs"], it["op"]
+        assert_bits_equal(to_host(it["l"], dt), oracle.bcast(f, dt, bs, it["root"], it["leaf"], op),
+                          f"tuned batch bcast {f.name} {c}")
+        want = oracle.reduce(f, dt, bs, it["leaf"], it["root"], op)
+        got = to_host(it["r2"], dt)
+        if c["mode"] == "atomic" and op == "SUM" and dt.startswith("fp"):
+            assert_atomic_sum_close(got, want, f, dt, bs, it["leaf"], it["root"], f"tuned batch reduce {f.name}")
+        else:
+            assert_bits_equal(got, want, f"tuned batch reduce {f.name} {c}")

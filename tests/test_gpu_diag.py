@@ -22,12 +22,16 @@ FORESTS = [sfgen.owned_plus_ghosts(5), sfgen.owned_plus_ghosts(6, keep=0.6),
 _SF = {}
 
 
-def sf_for(f):
+PLANS = ["diagonal", "diagonal_staged"]
+
+
+def sf_for(f, plan="diagonal"):
     if f.name not in _SF:
         sf = StarForest.from_forest(f).setup().set_mode("deterministic")
         assert sf.info()["dg_chunks"] > 0
+        assert sf.tuning()["reduce_plan"] == "root_major"   # the default
         _SF[f.name] = sf
-    return _SF[f.name]
+    return _SF[f.name].set_reduce_plan(plan)
 
 
 # one vector per unit: bs = 1, or 16-byte units
@@ -35,11 +39,13 @@ UNITS = [("fp64", 1), ("fp32", 1), ("bf16", 1), ("int32", 1), ("int64", 1),
          ("fp64", 2), ("fp32", 4), ("bf16", 8), ("int32", 4), ("int64", 2)]
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
 @pytest.mark.parametrize("op", ["SUM", "MIN", "MAX"])
 @pytest.mark.parametrize("dtype,bs", UNITS)
-def test_diagonal_chunk_reduce_bit_exact(f, op, dtype, bs):
-    sf = sf_for(f)
+def test_diagonal_chunk_reduce_bit_exact(f, op, dtype, bs, plan):
+    sf = sf_for(f, plan)
+    assert sf.tuning()["reduce_plan"] == plan
     kind = "wide" if dtype.startswith("int") else "signed"
     root, leaf = make_data(f, dtype, bs, 1500, kind, kind)
     want = oracle.reduce(f, dtype, bs, leaf, root, op)
@@ -47,16 +53,38 @@ def test_diagonal_chunk_reduce_bit_exact(f, op, dtype, bs):
     for call in range(2):
         r = to_dev(root, dtype)
         sf.reduce(l, r, op, bs=bs)
-        assert_bits_equal(to_host(r, dtype), want, f"diag reduce {f.name} {op} {dtype}x{bs} call {call}")
+        assert_bits_equal(to_host(r, dtype), want, f"diag reduce {plan} {f.name} {op} {dtype}x{bs} call {call}")
     assert_bits_equal(to_host(l, dtype), leaf, "leafdata must be untouched")
     assert sf.device_status() == 0
+
+
+@pytest.mark.parametrize("op", ["SUM", "MAX"])
+def test_plans_agree_and_tuner_keeps_the_bits(op):
+    """Every plan gives the same bits; the tuner may pick any of them and still does."""
+    f = FORESTS[3]
+    sf = sf_for(f, "auto")
+    root, leaf = make_data(f, "fp64", 1, 1520, "signed", "signed")
+    want = oracle.reduce(f, "fp64", 1, leaf, root, op)
+    l = to_dev(leaf, "fp64")
+    for plan in ["root_major"] + PLANS:
+        r = to_dev(root, "fp64")
+        sf.set_reduce_plan(plan).reduce(l, r, op)
+        assert_bits_equal(to_host(r, "fp64"), want, f"plan {plan} {op}")
+    sf.set_reduce_plan("auto")
+    choice = sf.autotune("reduce", l, to_dev(root, "fp64"), op, reps=2)
+    assert choice == "deterministic"
+    assert sf.tuning()["reduce_plan"] in ["root_major"] + PLANS
+    r = to_dev(root, "fp64")
+    sf.reduce(l, r, op)
+    assert_bits_equal(to_host(r, "fp64"), want, f"tuned plan {sf.tuning()['reduce_plan']} {op}")
+    sf.set_reduce_plan("diagonal")
 
 
 @pytest.mark.parametrize("dtype,bs", [("fp64", 3), ("bf16", 2), ("int32", 1)])
 def test_other_units_and_replace_keep_the_root_major_plan(dtype, bs):
     """Units of several vectors, and REPLACE, run the root-major plan of every root."""
     f = FORESTS[0]
-    sf = sf_for(f)
+    sf = sf_for(f, "diagonal_staged")
     for op in ("REPLACE", "SUM", "MAX"):
         root, leaf = make_data(f, dtype, bs, 1501)
         r, l = to_dev(root, dtype), to_dev(leaf, dtype)
@@ -64,10 +92,11 @@ def test_other_units_and_replace_keep_the_root_major_plan(dtype, bs):
         assert_bits_equal(to_host(r, dtype), oracle.reduce(f, dtype, bs, leaf, root, op), f"{op} {dtype}x{bs}")
 
 
-def test_signed_zero_ties_on_diagonal_chunks():
+@pytest.mark.parametrize("plan", PLANS)
+def test_signed_zero_ties_on_diagonal_chunks(plan):
     """Two- and three-leaf roots of +0 / -0 leaves: the diagonal leaf keeps its canonical place."""
     f = FORESTS[0]
-    sf = sf_for(f)
+    sf = sf_for(f, plan)
     ro, lo = oracle.layout(f)
     sgn = sfgen.rng.u64(1502, 1, int(lo[-1])) & np.uint64(1)
     leaf = np.where(sgn == 1, -0.0, 0.0)
@@ -109,13 +138,14 @@ def negative_offset_forest():
                         name="negative_offset")
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("dtype,bs", [("fp64", 1), ("fp32", 1), ("bf16", 1), ("fp64", 2), ("int64", 1)])
-def test_negative_offset_and_unaligned_buffers(dtype, bs):
+def test_negative_offset_and_unaligned_buffers(dtype, bs, plan):
     """A negative diagonal offset, and buffers that are not 16-byte aligned (one element into a
-    larger allocation: the Reduce then reads with plain loads instead of bulk copies), give the
+    larger allocation: the staged plan then reads with plain loads instead of bulk copies), give the
     oracle's bits; so does the Reduce from zero."""
     f = negative_offset_forest()
-    sf = StarForest.from_forest(f).setup().set_mode("deterministic")
+    sf = StarForest.from_forest(f).setup().set_mode("deterministic").set_reduce_plan(plan)
     info = sf.info()
     assert info["dg_chunks"] > 0 and info["dg_rest_roots"] > 0
     root, leaf = make_data(f, dtype, bs, 1601)
