@@ -82,7 +82,8 @@ enum { SF_MODE_AUTO = 0, SF_MODE_ATOMIC = 1, SF_MODE_DETERMINISTIC = 2 };
  * THREE_PHASE: pack remote edges into a root buffer, move each (root rank -> leaf rank) chunk
  *   into a leaf buffer, unpack into leafdata; self edges are scattered directly.
  * ROOT_MAJOR: each root unit is read once and written to all of its leaves.
- * AUTO: the library picks (FUSED, or what sf_autotune measured fastest). */
+ * AUTO: what sf_autotune measured fastest, else ROOT_MAJOR for units of 64 bytes or more on
+ *   forests with at least 4 leaves per connected root on average, else FUSED. */
 enum { SF_PATH_AUTO = 0, SF_PATH_FUSED = 1, SF_PATH_THREE_PHASE = 2, SF_PATH_ROOT_MAJOR = 3 };
 
 /* Plans of the deterministic Reduce of one-vector units (SUM/MIN/MAX; results are identical):
@@ -191,7 +192,7 @@ int sf_set_vector_bytes(sf_t *sf, int32_t bytes);
 int sf_set_tile_edges(sf_t *sf, int32_t edges);
 
 typedef struct {
-  int32_t path;          /* SF_PATH_* the Bcast runs (AUTO resolved) */
+  int32_t path;          /* SF_PATH_* the Bcast runs (AUTO resolved; for units under 64 bytes) */
   int32_t mode;          /* SF_MODE_* the Reduce runs (AUTO resolved) */
   int32_t vector_bytes;  /* 0 = 16 */
   int32_t tile_edges;    /* edges per two-sided tile */

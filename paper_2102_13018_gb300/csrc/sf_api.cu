@@ -218,7 +218,7 @@ DgArgs dg_args(const sf_t *sf, const void *leaf, void *root) {
 
 int reduce_det_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int vbo,
                       int nv, void *partial, int32_t *counter, bool zero_root) {
-  const bool nv1 = reduce_nv1(op, vbo, nv);
+  const bool nv1 = reduce_nv1(op, vbo, nv), flat = reduce_flat(op, vbo, nv);
   const DevPlan *d = &sf->dp;
   if (reduce_dg(sf, op, nv)) {
     DgArgs g = dg_args(sf, leaf, root);
@@ -237,14 +237,15 @@ int reduce_det_launch(sf_t *sf, const sf_unit &u, const void *leaf, void *root, 
     if (!sf->has_rest) return SF_SUCCESS;
     d = &sf->dp_rest;   // the roots the chunks leave out
   }
-  const RmTile *tiles = op == SF_REPLACE ? d->rm_winner_tiles : nv1 ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
-  const int nt = op == SF_REPLACE ? d->n_rm_winner_tiles : nv1 ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
+  const bool nv1_list = nv1 || flat;
+  const RmTile *tiles = op == SF_REPLACE ? d->rm_winner_tiles : nv1_list ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
+  const int nt = op == SF_REPLACE ? d->n_rm_winner_tiles : nv1_list ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
   if (nt == 0) return SF_SUCCESS;
   RmArgs a = rm_args_plan(sf, *d, tiles, nt, root, const_cast<void *>(leaf), nullptr, nv);
   a.partial = partial;
   a.counter = counter;
   a.zero_root = zero_root;
-  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1}));
+  return launched(launch_rm(u.dtype, op, vbo, RM_REDUCE, RmLaunch{&a, nullptr, nullptr, nt, s, nv1, flat}));
 }
 
 // Zero the roots without leaves (and their argleaf entries, if given) for an operation that
@@ -301,7 +302,13 @@ int fetch_launch(sf_t *sf, const sf_unit &u, void *root, const void *leaf, void 
   return launched(launch_rm(u.dtype, op, vbo, RM_FETCH, a, sf->dp.n_rm_fetch_tiles, s));
 }
 
-int bcast_path(const sf_t *sf) { return sf->path == SF_PATH_AUTO ? sf->tuned_path : sf->path; }
+int bcast_path(const sf_t *sf, int64_t unit_bytes) {
+  if (sf->path != SF_PATH_AUTO) return sf->path;
+  if (sf->path_tuned) return sf->tuned_path;
+  return unit_bytes >= kRootMajorUnitBytes && sf->info.nedges >= kRootMajorMeanDegree * sf->info.connected_roots
+             ? SF_PATH_ROOT_MAJOR
+             : SF_PATH_FUSED;
+}
 int reduce_mode(const sf_t *sf) { return sf->mode == SF_MODE_AUTO ? sf->tuned_mode : sf->mode; }
 
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op) {
@@ -552,7 +559,7 @@ int sf_set_tile_edges(sf_t *sf, int32_t edges) {
 
 int sf_get_tuning(const sf_t *sf, sf_tuning *out) {
   if (!sf || !out) return SF_ERR_NULL;
-  out->path = bcast_path(sf);
+  out->path = bcast_path(sf, 0);
   out->mode = reduce_mode(sf);
   out->vector_bytes = sf->vec_bytes;
   out->tile_edges = sf->tile_edges ? sf->tile_edges : int32_t(sf->info.ts_tile_edges);
@@ -569,7 +576,8 @@ int sf_bcast_begin(sf_t *sf, sf_unit unit, const void *rootdata, void *leafdata,
     return rc;
   if (find_pending(sf, K_BCAST, unit, rootdata, leafdata, nullptr, op, 0, 0)) return SF_ERR_PENDING;
   int finish = 0;
-  if ((rc = bcast_launch(sf, unit, rootdata, leafdata, op, static_cast<cudaStream_t>(stream), bcast_path(sf), &finish)))
+  if ((rc = bcast_launch(sf, unit, rootdata, leafdata, op, static_cast<cudaStream_t>(stream),
+                         bcast_path(sf, int64_t(w) * unit.bs), &finish)))
     return rc;
   sf->pending.push_back(Pending{K_BCAST, unit, rootdata, leafdata, nullptr, op, 0, 0, finish});
   return SF_SUCCESS;
@@ -692,7 +700,9 @@ int sf_bcast_with_memtype_begin(sf_t *sf, sf_unit unit, int32_t rootmtype, const
     dleaf = sf->stage_leaf.p;
   }
   int finish = 0;
-  if ((rc = bcast_launch(sf, unit, droot, dleaf, op, s, bcast_path(sf), &finish))) return rc;
+  if ((rc = bcast_launch(sf, unit, droot, dleaf, op, s, bcast_path(sf, int64_t(elem_size(unit.dtype)) * unit.bs),
+                         &finish)))
+    return rc;
   sf->pending.push_back(Pending{K_BCAST_MT, unit, rootdata, leafdata, nullptr, op, rootmtype, leafmtype, finish});
   return SF_SUCCESS;
 }

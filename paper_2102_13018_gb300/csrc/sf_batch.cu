@@ -97,7 +97,7 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
       return rc;
     if (sf->info.nedges == 0) continue;
     if (o.kind == SF_OP_BCAST) {
-      const int path = bcast_path(sf);
+      const int path = bcast_path(sf, ub);
       paths[i] = path;
       const int vb = pick_vb_sf(sf, w, ub, true, {root, leaf});
       if (!vb) return SF_ERR_ALIGN;
@@ -243,7 +243,8 @@ bool choices_changed(const sf_batch_t *b) {
   for (size_t i = 0; i < b->ops.size(); ++i) {
     const sf_batch_op &o = b->ops[i];
     if (o.kind == SF_OP_BARRIER) continue;
-    if (o.kind == SF_OP_BCAST && bcast_path(o.sf) != b->paths[i]) return true;
+    if (o.kind == SF_OP_BCAST && bcast_path(o.sf, int64_t(elem_size(o.unit.dtype)) * o.unit.bs) != b->paths[i])
+      return true;
     if (o.kind == SF_OP_REDUCE && reduce_mode(o.sf) != b->modes[i]) return true;
     const auto &c = b->scratch[i];
     if (c.partial != o.sf->partial.p || c.counter != o.sf->counter.p || c.ts_tiles != o.sf->dp.ts_tiles ||
@@ -398,7 +399,10 @@ int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst
   }
   sf->vec_bytes = best_c.vec;
   if ((rc = sf_set_tile_edges(sf, best_c.edges))) return rc;
-  if (kind == SF_OP_BCAST) sf->tuned_path = best_c.c;
+  if (kind == SF_OP_BCAST) {
+    sf->tuned_path = best_c.c;
+    sf->path_tuned = true;
+  }
   else sf->tuned_mode = best_c.c;
   if (kind == SF_OP_REDUCE && best_c.c == SF_MODE_DETERMINISTIC && plan0 == SF_PLAN_AUTO && best_c.plan != SF_PLAN_AUTO)
     sf->tuned_plan = best_c.plan;

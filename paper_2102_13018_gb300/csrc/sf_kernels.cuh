@@ -794,6 +794,75 @@ __device__ __forceinline__ void fold_tile_flat(const RmArgs &a, const RmTile &t,
   }
 }
 
+// Gather-then-fold for units of nv > 1 vectors (FLAT kernels; Reduce SUM/MIN/MAX): the tile's
+// blocks are taken in groups of at most NIT * kThreads (block, vector) items, a thread holding up
+// to NIT of them (4, or 2 for 16-byte vectors, whose packs would spill at four).  For each group the CTA copies the leaf vectors of the
+// group's entries into s_val by cp.async -- R / nv whole leaf units per round, every vector of
+// the round in flight at once whatever the blocks' lengths -- and each item folds its block's
+// entries of the round from shared memory in canonical order, carrying its accumulator across
+// rounds (the same left fold as fold_block).  Every thread of the CTA calls this.
+template <typename T, int VB, int OP, bool ZR>
+__device__ __forceinline__ void fold_tile_flat_nv(const RmArgs &a, const RmTile &t, const BlockRec *s_rec, int32_t r0,
+                                                  const int32_t *s_leaf, int32_t l0, Pack<T, VB> *s_val) {
+  using A = typename Acc<T, OP>::type;
+  constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;
+  constexpr int NIT = VB >= 16 ? 2 : 4;                  // items per thread
+  static_assert(NIT * kThreads >= RM_FLAT_MAX_NV, "a group holds at least one block");
+  constexpr int R = RM_FLAT_BYTES / VB;                  // leaf vectors per round
+  const int32_t nv = a.nv;                               // 1 < nv <= min(R, RM_FLAT_MAX_NV)
+  const int32_t gb = NIT * kThreads / nv;                // blocks per group
+  const int32_t rl = R / nv;                             // leaf units per round
+  const int32_t *idx = s_leaf + (t.k0 - l0);             // idx[i]: leaf unit of entry k0 + i
+  const BlockRec *rec = s_rec + (t.a - r0);              // rec[w]: block a + w (rec[cnt]: the next one)
+  const char *leaf = static_cast<const char *>(a.leaf);
+  for (int32_t g0 = 0; g0 < t.cnt; g0 += gb) {
+    const int32_t g1 = min(t.cnt, g0 + gb), nitems = (g1 - g0) * nv;
+    int32_t bw[NIT], vv[NIT];
+    Pack<T, VB> xr[NIT];
+    Pack<A, AVB> acc[NIT];
+#pragma unroll
+    for (int j = 0; j < NIT; ++j) {
+      const int32_t it = threadIdx.x + j * kThreads;
+      bw[j] = -1;
+      if (it < nitems) {
+        const int32_t q = div_by(it, a.nv_m, a.nv_s);
+        bw[j] = g0 + q;
+        vv[j] = it - q * nv;
+        if (rec[bw[j]].who >= 0) xr[j] = ld_root<T, VB>(a.root, int64_t(rec[bw[j]].who) * nv + vv[j], ZR);
+      }
+    }
+    const int32_t e0 = int32_t(rec[g0].e0 - t.k0), e1 = int32_t(rec[g1].e0 - t.k0);   // the group's entries
+    for (int32_t q0 = e0; q0 < e1; q0 += rl) {
+      const int32_t nq = min(rl, e1 - q0), nvec = nq * nv;
+      if (q0 > e0) __syncthreads();   // the previous round's vectors are folded
+      for (int32_t k = threadIdx.x; k < nvec; k += kThreads) {
+        const int32_t e = div_by(k, a.nv_m, a.nv_s), v = k - e * nv;
+        cp_async_vec<VB>(s_val + k, leaf + (int64_t(idx[q0 + e]) * nv + v) * VB);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NIT; ++j) {
+        if (bw[j] < 0) continue;
+        const int32_t b0 = int32_t(rec[bw[j]].e0 - t.k0), b1 = int32_t(rec[bw[j] + 1].e0 - t.k0);
+        const int32_t lo = max(b0, q0), hi = min(b1, q0 + nq);
+        for (int32_t i = lo; i < hi; ++i) {
+          const Pack<T, VB> y = s_val[(i - q0) * nv + vv[j]];
+#pragma unroll
+          for (int l = 0; l < Pack<T, VB>::L; ++l)
+            acc[j].v[l] = i == b0 ? to_acc<A, T>(y.v[l]) : combine<OP, A>(acc[j].v[l], to_acc<A, T>(y.v[l]));
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NIT; ++j)
+      if (bw[j] >= 0)
+        fold_finish<T, VB, OP>(a.root, a.combs, a.partial, a.counter, nv, load_block(rec, a.combs, bw[j]), vv[j], acc[j],
+                               xr[j], ZR);
+    __syncthreads();   // s_val is free for the next group
+  }
+}
+
 // NB single-block roots folded together (Reduce SUM/MIN/MAX): NB descriptors, then U leaf
 // indices per root, then U leaf values per root are in flight at once, so each thread keeps NB
 // independent load chains going; each root still folds its leaves in canonical order.
@@ -845,10 +914,13 @@ __device__ __forceinline__ void fold_many(void *root, void *leaf, const int32_t 
 // so the multi-vector fold code is left out and the kernel fits a smaller register budget.
 // ZR: a Reduce from zero (RmArgs.zero_root set; the roots count as 0 and are never read) --
 // a template parameter, so the plain Reduce's unrolled root loads carry no branch.
-template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false>
+// FLAT: units of several vectors whose chunk tiles fold by gather-then-fold (fold_tile_flat_nv);
+// it reads the tiles of rm_fold_nv1_tiles, as NV1 does.
+template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false, bool FLAT = false>
 __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   static_assert(!NV1 || (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4), "NV1 is a Reduce-op form");
   static_assert(!ZR || (MODE == RM_REDUCE && OP != OP_REPLACE), "ZR is a Reduce-op form");
+  static_assert(!FLAT || (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4 && !NV1), "FLAT is a Reduce-op form");
   using A = typename Acc<T, OP>::type;
   constexpr int AVB = int(sizeof(A)) * Pack<T, VB>::L;   // accumulator pack bytes
   constexpr int U = VB >= 16 ? 2 : 4;
@@ -960,7 +1032,7 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       // memory by two bulk copies (spans widened to 16-byte boundaries), so each fold issues
       // only its data loads.  NB work items per thread, folded together when all are
       // single-block roots.
-      constexpr int kStageLeaves = NV1 ? RM_STAGE_LEAVES_NV1 : RM_STAGE_LEAVES;
+      constexpr int kStageLeaves = NV1 || FLAT ? RM_STAGE_LEAVES_NV1 : RM_STAGE_LEAVES;
       __shared__ alignas(16) BlockRec s_rec[RM_STAGE_RECS];
       __shared__ alignas(16) int32_t s_leaf[kStageLeaves];
       __shared__ alignas(8) uint64_t s_bar;
@@ -973,10 +1045,14 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
       }
       const bool staged = stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf,
                                  a.m_leaf + l0, uint32_t(l1 - l0) * 4u, &s_bar, a.status);
-      if constexpr (NV1) {   // one vector per unit: gather-then-fold (the CTA agrees on the stage first)
+      if constexpr (NV1 || FLAT) {   // gather-then-fold (the CTA agrees on the stage first)
         __shared__ alignas(16) unsigned char s_val[RM_FLAT_BYTES];
-        if (__syncthreads_and(staged))
-          fold_tile_flat<T, VB, OP, ZR>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+        if (__syncthreads_and(staged)) {
+          if constexpr (NV1)
+            fold_tile_flat<T, VB, OP, ZR>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+          else
+            fold_tile_flat_nv<T, VB, OP, ZR>(a, t, s_rec, r0, s_leaf, l0, reinterpret_cast<Pack<T, VB> *>(s_val));
+        }
         return;
       } else {
         if (!staged) return;
@@ -1018,11 +1094,11 @@ __device__ __forceinline__ void rm_tile(const RmArgs &a, const RmTile &t) {
   }
 }
 
-template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false>
-__global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
+template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool ZR = false, bool FLAT = false>
+__global__ void __launch_bounds__(kThreads, (NV1 || FLAT ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
     rm_kernel(RmArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
-  rm_tile<T, VB, OP, MODE, NV1, ZR>(a, t);
+  rm_tile<T, VB, OP, MODE, NV1, ZR, FLAT>(a, t);
 }
 
 // ------------------------------------------------------------------ diagonal-chunk Reduce

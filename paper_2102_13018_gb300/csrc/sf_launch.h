@@ -24,6 +24,7 @@ struct RmLaunch {
   int ntiles;
   cudaStream_t s;
   bool nv1 = false;   // the one-vector-unit Reduce kernel (reduce_nv1); its tiles come from rm_fold_nv1_tiles
+  bool flat = false;  // the gather-then-fold Reduce kernel of multi-vector units (reduce_flat); same tiles
 };
 
 // The diagonal-chunk Reduce: one forest (`single`, with `grid` CTAs looping over its tiles) or

@@ -61,6 +61,7 @@ struct sf_s {
   int32_t mode = SF_MODE_AUTO, path = SF_PATH_AUTO;
   int32_t tuned_mode = SF_MODE_DETERMINISTIC;   // what AUTO means (sf_autotune may change it)
   int32_t tuned_path = SF_PATH_FUSED;
+  bool path_tuned = false;           // sf_autotune chose tuned_path (else AUTO follows bcast_path's rule)
   int32_t plan = SF_PLAN_AUTO;       // deterministic Reduce plan (SF_PLAN_*)
   int32_t tuned_plan = SF_PLAN_ROOT_MAJOR;   // what SF_PLAN_AUTO means (sf_autotune may change it)
   int32_t vec_bytes = 0;             // widest vector of the Bcast / Reduce kernels (0: 16 bytes)
@@ -115,11 +116,24 @@ int reduce_mode(const sf_t *sf);   // SF_MODE_ATOMIC or SF_MODE_DETERMINISTIC af
 // the diagonal chunks.
 constexpr int64_t kOrderFreeMaxDegree = 1024;
 bool reduce_atomic(const sf_t *sf, int32_t dtype, int32_t op);
-int bcast_path(const sf_t *sf);    // SF_PATH_* after resolving AUTO
+// SF_PATH_* after resolving AUTO for units of unit_bytes: the tuned path, else ROOT_MAJOR for
+// units of kRootMajorUnitBytes or more on forests whose connected roots average
+// kRootMajorMeanDegree leaves or more (each root unit read once, whole-sector leaf writes), else
+// FUSED.  Measured on the 2^20-root power-law forest (8.8 leaves per root), bs = 64 fp32: 0.39 ms
+// root-major against 0.54 ms fused.
+constexpr int64_t kRootMajorUnitBytes = 64;
+constexpr int64_t kRootMajorMeanDegree = 4;
+int bcast_path(const sf_t *sf, int64_t unit_bytes);
 // Whether a root-major Reduce with `op`, vector width vbo and nv vectors per unit runs the
 // one-vector-unit kernel (NV1), which reads the rm_fold_nv1_tiles list; every caller takes the
 // tile list and the launch flag from this one test.
 inline bool reduce_nv1(int32_t op, int vbo, int nv) { return op != SF_REPLACE && nv == 1 && vbo >= 4; }
+// Whether a root-major Reduce of multi-vector units runs the gather-then-fold kernel (FLAT),
+// which reads rm_fold_nv1_tiles as NV1 does: SUM/MIN/MAX, vectors of 4 bytes or more, at most
+// RM_FLAT_MAX_NV vectors and RM_FLAT_BYTES per unit.
+inline bool reduce_flat(int32_t op, int vbo, int nv) {
+  return op != SF_REPLACE && vbo >= 4 && nv >= 2 && nv <= RM_FLAT_MAX_NV && nv * vbo <= RM_FLAT_BYTES;
+}
 // Enqueue a whole operation (begin and end) on `s`; used by sf_autotune.
 int bcast_all(sf_t *sf, const sf_unit &u, const void *root, void *leaf, int32_t op, cudaStream_t s, int path);
 int reduce_all(sf_t *sf, const sf_unit &u, const void *leaf, void *root, int32_t op, cudaStream_t s, int mode);

@@ -39,6 +39,9 @@ constexpr int RM_STAGE_LEAVES_NV1 = RM_TILE_CHUNK_EDGES_NV1 + 8;
 // Leaf vectors an NV1 chunk tile gathers into shared memory per round (bytes): with its two
 // stages the kernel stays within 48 KB of static shared memory, and four CTAs fit one SM.
 constexpr int RM_FLAT_BYTES = 22 * 1024;
+// Multi-vector units fold the same way (FLAT kernels) with up to this many vectors per unit
+// (a CTA of 256 threads holds 2 or 4 (block, vector) items per thread; a round holds whole units).
+constexpr int RM_FLAT_MAX_NV = 512;
 // Device status bits (sf_get_device_status): a bounded wait that ran out; a chunk tile larger
 // than the kernel's stage (a tile list that does not belong to the kernel) that was skipped.
 constexpr int32_t DEVSTAT_STAGE_TIMEOUT = 1;
