@@ -22,7 +22,8 @@ struct Group {
   int stage;
   int family;   // 0 two-sided kernel, 1 root-major kernel, 2 diagonal-chunk Reduce
   int dtype, op, vb, mode;
-  bool l2r, atomic;   // two-sided kernel; for the root-major kernel l2r marks one vector per unit
+  bool l2r, atomic;   // two-sided kernel
+  int rm_form;        // root-major Reduce kernel: 0 general, 1 one vector per unit, 2 gather-then-fold
   size_t tiles_off;   // BatchTile offset in the tile table
   int ntiles;
 };
@@ -147,17 +148,17 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
           for (int32_t t = 0; t < dg.back().ntiles; ++t) g.push_back(BatchTile{idx, t, nullptr});
           d = sf->has_rest ? &sf->dp_rest : nullptr;
         }
-        // one vector per unit: the group runs the Reduce kernel without the multi-vector fold,
-        // on the forest's chunk tiles cut for it
-        const bool nv1 = reduce_nv1(o.op, vbo, nv);
+        // one vector per unit, or a few (gather-then-fold): the group runs the Reduce kernel of
+        // that form, on the forest's chunk tiles cut for it
+        const bool nv1 = reduce_nv1(o.op, vbo, nv), flat = reduce_flat(o.op, vbo, nv), l1 = nv1 || flat;
         const int nt = !d ? 0 : o.op == SF_REPLACE ? d->n_rm_winner_tiles
-                                                   : nv1 ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
+                                                   : l1 ? d->n_rm_fold_nv1_tiles : d->n_rm_fold_tiles;
         if (nt > 0) {
-          const RmTile *rt = o.op == SF_REPLACE ? d->rm_winner_tiles : nv1 ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
+          const RmTile *rt = o.op == SF_REPLACE ? d->rm_winner_tiles : l1 ? d->rm_fold_nv1_tiles : d->rm_fold_tiles;
           const int idx = int(rm.size());
           rm.push_back(rm_args_plan(sf, *d, rt, nt, const_cast<void *>(root), const_cast<void *>(leaf), nullptr, nv));
           rm_src.push_back(i);
-          auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, int(nv1), 0}];
+          auto &g = grouped[{stage, 1, o.unit.dtype, o.op, vbo, RM_REDUCE, nv1 ? 1 : flat ? 2 : 0, 0}];
           for (int32_t t = 0; t < nt; ++t) g.push_back(BatchTile{idx, 0, rt + t});
         }
       }
@@ -180,7 +181,8 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
     g.op = std::get<3>(k);
     g.vb = std::get<4>(k);
     g.mode = std::get<5>(k);
-    g.l2r = std::get<6>(k);
+    g.l2r = g.family == 0 && std::get<6>(k) != 0;
+    g.rm_form = g.family == 1 ? std::get<6>(k) : 0;
     g.atomic = std::get<7>(k);
     g.tiles_off = tiles.size();
     g.ntiles = int(kv.second.size());
@@ -231,7 +233,7 @@ int launch_groups(sf_batch_t *b, cudaStream_t s) {
       e = launch_dg(g.dtype, g.op, g.vb, DgLaunch{nullptr, b->dg_ops, b->tiles + g.tiles_off, g.ntiles, g.ntiles, s});
     else
       e = launch_rm(g.dtype, g.op, g.vb, g.mode,
-                    RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.family == 1 && g.l2r != 0});
+                    RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.rm_form == 1, g.rm_form == 2});
     int rc;
     if ((rc = launched(e))) return rc;
   }

@@ -1691,13 +1691,13 @@ __global__ void __launch_bounds__(kThreads, (MinBlocks<OP, VB, ATOMIC>::value))
   ts_tile<T, VB, OP, L2R, ATOMIC, FETCH>(a, t);
 }
 
-template <typename T, int VB, int OP, int MODE, bool NV1 = false>
-__global__ void __launch_bounds__(kThreads, (NV1 ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
+template <typename T, int VB, int OP, int MODE, bool NV1 = false, bool FLAT = false>
+__global__ void __launch_bounds__(kThreads, (NV1 || FLAT ? RM_NV1_BLOCKS : MinBlocks<OP, VB, MODE == RM_FETCH>::value))
     rm_batch_kernel(const RmArgs *ops, const BatchTile *tiles) {
   const BatchTile bt = tiles[blockIdx.x];
   const RmArgs a = ops[bt.op];
   const RmTile t = *static_cast<const RmTile *>(bt.tile);
-  rm_tile<T, VB, OP, MODE, NV1>(a, t);
+  rm_tile<T, VB, OP, MODE, NV1, false, FLAT>(a, t);
 }
 
 template <typename T, int VB, int OP>

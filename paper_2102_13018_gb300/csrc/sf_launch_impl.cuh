@@ -33,9 +33,13 @@ cudaError_t go_rm(const RmLaunch &L) {
       return cudaErrorInvalidValue;
     }
   }
-  if (L.flat) {   // multi-vector units, gather-then-fold; a single forest's rm_fold_nv1_tiles
+  if (L.flat) {   // multi-vector units, gather-then-fold, on rm_fold_nv1_tiles
     if constexpr (MODE == RM_REDUCE && OP != OP_REPLACE && VB >= 4) {
-      if (L.tiles || L.single->nv < 2 || L.single->nv > RM_FLAT_MAX_NV || L.single->nv * VB > RM_FLAT_BYTES)
+      if (L.tiles) {   // the batch builder checked every operation's unit (reduce_flat)
+        rm_batch_kernel<T, VB, OP, MODE, false, true><<<L.ntiles, kThreads, 0, L.s>>>(L.ops, L.tiles);
+        return cudaGetLastError();
+      }
+      if (L.single->nv < 2 || L.single->nv > RM_FLAT_MAX_NV || L.single->nv * VB > RM_FLAT_BYTES)
         return cudaErrorInvalidValue;
       if (zr) rm_kernel<T, VB, OP, MODE, false, true, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
       else rm_kernel<T, VB, OP, MODE, false, false, true><<<L.ntiles, kThreads, 0, L.s>>>(*L.single);
