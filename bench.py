@@ -522,6 +522,95 @@ def run_autograd(flush, peak):
                         "bs=64; forward + backward of Bcast, Reduce SUM and Reduce MAX", **out}
 
 
+def run_e2e(sf, x_h, y_h, lvec, stream, step_bytes, world, Ke):
+    """End to end with x and y in pinned host memory, two ways, each step copying its x and y in
+    (H2D) and its result y out (D2H) inside the timed region:
+      pipelined (the reported value): independent steps y_k = y + Reduce(Bcast x) through
+        sf.bcast / sf.reduce on device buffers, double-buffered over four streams (x in, y in,
+        kernels, y out), so step k's D2H, step k+1's kernels and step k+2's H2D overlap;
+      serial: sf_*_with_memtype on the host buffers, the host waiting for y after every step."""
+    import torch
+    nr = sf.nroots_total
+    xh = torch.from_numpy(x_h).pin_memory()
+    yh = torch.from_numpy(y_h).pin_memory()
+    yo = [torch.empty_like(yh).pin_memory() for _ in range(2)]
+    h2d, d2h = 8 * nr + 8 * nr, 8 * nr
+    # serial, through the memtype calls
+    for _ in range(2):
+        sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
+        sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
+        sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = e0.elapsed_time(e1) / Ke
+    # pipelined (x and y copied in on two streams, each on its own copy engine)
+    s_in, s_in2, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    xd = [torch.empty(nr, dtype=torch.float64, device="cuda") for _ in range(2)]
+    yd = [torch.empty(nr, dtype=torch.float64, device="cuda") for _ in range(2)]
+    lv = [lvec, torch.empty_like(lvec)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_in2 = [torch.cuda.Event() for _ in range(2)]
+    ev_c = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def steps(n, t0=None):
+        for k in range(n):
+            b = k & 1
+            if k >= 2:
+                for si in (s_in, s_in2):
+                    si.wait_event(ev_c[b])     # step k-2's kernels are done with xd[b], yd[b]
+                    si.wait_event(ev_out[b])   # and its y has left yd[b]
+            if k == 0 and t0 is not None:
+                t0.record(s_in)
+                s_in2.wait_event(t0)
+            with torch.cuda.stream(s_in):
+                xd[b].copy_(xh, non_blocking=True)
+            with torch.cuda.stream(s_in2):
+                yd[b].copy_(yh, non_blocking=True)
+            ev_in[b].record(s_in)
+            ev_in2[b].record(s_in2)
+            stream.wait_event(ev_in[b])
+            stream.wait_event(ev_in2[b])
+            if k >= 2:
+                stream.wait_event(ev_out[b])
+            sf.bcast(xd[b], lv[b], "REPLACE", stream=stream)
+            sf.reduce(lv[b], yd[b], "SUM", stream=stream)
+            ev_c[b].record(stream)
+            s_out.wait_event(ev_c[b])
+            if k >= 2:
+                s_out.wait_event(ev_out[b])
+            with torch.cuda.stream(s_out):
+                yo[b].copy_(yd[b], non_blocking=True)
+            ev_out[b].record(s_out)
+
+    steps(3)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps(Ke, p0)
+    p1.record(s_out)
+    torch.cuda.synchronize()
+    pipe_ms = p0.elapsed_time(p1) / Ke
+    # the last step's result against the same step run serially on the device
+    ref = yh.cuda()
+    sf.bcast(xh.cuda(), lvec, "REPLACE", stream=stream)
+    sf.reduce(lvec, ref, "SUM", stream=stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(ref.cpu(), yo[(Ke - 1) & 1]))
+    return {"value": world * step_bytes / (pipe_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": pipe_ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke, "result_bit_identical": same,
+            "what": "pinned host x, y in and y out every step; steps pipelined over four streams "
+                    "(x and y H2D, kernels, D2H overlap); sf.bcast + sf.reduce on device buffers",
+            "serial_memtype": {"ms_per_step": serial_ms,
+                               "value": world * step_bytes / (serial_ms * 1e-3) / 1e9,
+                               "what": "sf_*_with_memtype on the host buffers, host waits for y every step"}}
+
+
 def run_halo(flush, peak):
     """3-D halo exchange, 256^3 fp64 grid in 4x4x4 ranks, 27-point ghosts (about 1.2M ghost
     leaves): Bcast REPLACE (ghost update) and Reduce SUM (ghost accumulate) at bs = 1 and 5.
@@ -810,33 +899,11 @@ def main():
         sf.set_mode("deterministic")
         variants["fp32"] = run_fp32_step(sf, info, x, y, stream, flush, peak, max(3, min(K, 50)))
 
-    # end to end through the public API, as an SpMV caller runs the step: x and y in pinned host
-    # memory, the work vector lvec on the device (copies inside the timed region, the host
-    # waiting for y every step)
+    # end to end through the public API with the data in pinned host memory: every step copies
+    # its x and y in, runs Bcast + Reduce, and copies its y out
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(x_h).pin_memory()
-        yh = torch.from_numpy(y_h).pin_memory()
-        for _ in range(2):
-            sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
-            sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
-        torch.cuda.synchronize()
-        Ke = max(3, min(K, 50))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(Ke):
-            sf.bcast_memtype(xh, lvec, "REPLACE", stream=stream)
-            sf.reduce_memtype(lvec, yh, "SUM", stream=stream)
-            stream.synchronize()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / Ke
-        # Bcast: x in; Reduce: y in, y out
-        h2d = 8 * nr + 8 * nr
-        d2h = 8 * nr
-        e2e = {"value": world * (bb + rb) / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": Ke,
-               "what": "x, y pinned host (sf_*_with_memtype), lvec on the device, host waits for y every step"}
+        e2e = run_e2e(sf, x_h, y_h, lvec, stream, bb + rb, world, max(3, min(K, 50)))
 
     pingpong = None
     if not args.no_pingpong:
