@@ -57,6 +57,11 @@ struct sf_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // the variant groups of a stage are independent: they run side by side on these streams,
+  // forked from and joined back into the caller's stream (parallel branches in the graph)
+  static constexpr int kLanes = 4;
+  cudaStream_t lanes[kLanes] = {};
+  cudaEvent_t fork = nullptr, join[kLanes] = {};
 };
 
 namespace {
@@ -224,18 +229,63 @@ int build(sf_batch_t *b, const sf_batch_op *ops, int32_t n, cudaStream_t s) {
   return SF_SUCCESS;
 }
 
+int launch_group(const sf_batch_t *b, const Group &g, cudaStream_t s) {
+  cudaError_t e;
+  if (g.family == 0)
+    e = launch_ts(g.dtype, g.op, g.vb, g.l2r, g.atomic, false, TsLaunch{nullptr, b->ts_ops, b->tiles + g.tiles_off, g.ntiles, s});
+  else if (g.family == 2)
+    e = launch_dg(g.dtype, g.op, g.vb, DgLaunch{nullptr, b->dg_ops, b->tiles + g.tiles_off, g.ntiles, g.ntiles, s});
+  else
+    e = launch_rm(g.dtype, g.op, g.vb, g.mode,
+                  RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.rm_form == 1, g.rm_form == 2});
+  return launched(e);
+}
+
+int ensure_lanes(sf_batch_t *b) {
+  if (b->fork) return SF_SUCCESS;
+  int rc;
+  for (int l = 0; l < sf_batch_t::kLanes; ++l) {
+    if ((rc = cuda_err(cudaStreamCreateWithFlags(&b->lanes[l], cudaStreamNonBlocking)))) return rc;
+    if ((rc = cuda_err(cudaEventCreateWithFlags(&b->join[l], cudaEventDisableTiming)))) return rc;
+  }
+  return cuda_err(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+}
+
+// Stage by stage (the groups are sorted by stage): a stage of one group runs on `s`; the groups
+// of a larger stage go to the lanes, largest first onto the least loaded lane (by tiles), and
+// `s` waits for every lane used before the next stage.
 int launch_groups(sf_batch_t *b, cudaStream_t s) {
-  for (const Group &g : b->groups) {
-    cudaError_t e;
-    if (g.family == 0)
-      e = launch_ts(g.dtype, g.op, g.vb, g.l2r, g.atomic, false, TsLaunch{nullptr, b->ts_ops, b->tiles + g.tiles_off, g.ntiles, s});
-    else if (g.family == 2)
-      e = launch_dg(g.dtype, g.op, g.vb, DgLaunch{nullptr, b->dg_ops, b->tiles + g.tiles_off, g.ntiles, g.ntiles, s});
-    else
-      e = launch_rm(g.dtype, g.op, g.vb, g.mode,
-                    RmLaunch{nullptr, b->rm_ops, b->tiles + g.tiles_off, g.ntiles, s, g.rm_form == 1, g.rm_form == 2});
-    int rc;
-    if ((rc = launched(e))) return rc;
+  int rc;
+  const size_t ng = b->groups.size();
+  for (size_t i0 = 0; i0 < ng;) {
+    size_t i1 = i0;
+    while (i1 < ng && b->groups[i1].stage == b->groups[i0].stage) ++i1;
+    if (i1 - i0 == 1) {
+      if ((rc = launch_group(b, b->groups[i0], s))) return rc;
+      i0 = i1;
+      continue;
+    }
+    if ((rc = ensure_lanes(b)) || (rc = cuda_err(cudaEventRecord(b->fork, s)))) return rc;
+    std::vector<size_t> order;
+    for (size_t i = i0; i < i1; ++i) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return b->groups[x].ntiles > b->groups[y].ntiles; });
+    int64_t load[sf_batch_t::kLanes] = {};
+    bool used[sf_batch_t::kLanes] = {};
+    for (size_t i : order) {
+      int l = 0;
+      for (int k = 1; k < sf_batch_t::kLanes; ++k)
+        if (load[k] < load[l]) l = k;
+      if (!used[l] && (rc = cuda_err(cudaStreamWaitEvent(b->lanes[l], b->fork, 0)))) return rc;
+      used[l] = true;
+      load[l] += b->groups[i].ntiles;
+      if ((rc = launch_group(b, b->groups[i], b->lanes[l]))) return rc;
+    }
+    for (int l = 0; l < sf_batch_t::kLanes; ++l)
+      if (used[l] && ((rc = cuda_err(cudaEventRecord(b->join[l], b->lanes[l]))) ||
+                      (rc = cuda_err(cudaStreamWaitEvent(s, b->join[l], 0)))))
+        return rc;
+    i0 = i1;
   }
   return SF_SUCCESS;
 }
@@ -314,6 +364,11 @@ int sf_batch_destroy(sf_batch_t *b) {
   if (!b) return SF_SUCCESS;
   drop_graph(b);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (int l = 0; l < sf_batch_t::kLanes; ++l) {
+    if (b->lanes[l]) cudaStreamDestroy(b->lanes[l]);
+    if (b->join[l]) cudaEventDestroy(b->join[l]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   release(b->tables);
   delete b;
   return SF_SUCCESS;
