@@ -838,7 +838,22 @@ int sf_reduce_maxloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdat
   a.partial_arg = static_cast<int32_t *>(sf->partial_arg.p);
   a.counter = static_cast<int32_t *>(sf->counter.p);
   a.bs = unit.bs;
-  return launched(launch_maxloc(unit.dtype, a, sf->dp.n_rm_fold_tiles, s));
+  a.status = static_cast<int32_t *>(sf->status.p);
+  // gather-then-fold when the unit is vectors of 4, 8 or 16 bytes, no more than the kernel's
+  // items per CTA (a round of the 22 KB buffer holds a whole unit), else the general kernel
+  const int ub = w * unit.bs;
+  const int pv = pick_vb(w, ub, true, {leafdata, rootdata});
+  const int vb = pv == 16 ? 16 : w >= 4 ? w : 0;   // the vector widths the kernel is built for
+  const int nv = vb ? ub / vb : 0;
+  MaxlocFlat f{};
+  const int max_nv = vb >= 16 ? (w < 4 ? 256 : 512) : 1024;   // the kernel's items per CTA
+  if (vb >= 4 && nv >= 1 && nv <= max_nv && nv * vb <= RM_FLAT_BYTES) {
+    const DivMagic dm = div_magic(uint32_t(nv));
+    f = MaxlocFlat{nv, dm.m, dm.s};
+    a.tiles = sf->dp.rm_fold_nv1_tiles;
+    return launched(launch_maxloc(unit.dtype, a, sf->dp.n_rm_fold_nv1_tiles, vb, f, s));
+  }
+  return launched(launch_maxloc(unit.dtype, a, sf->dp.n_rm_fold_tiles, 0, f, s));
 }
 
 int sf_maxloc_scatter(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,

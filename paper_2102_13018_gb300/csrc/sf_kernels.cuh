@@ -1590,6 +1590,7 @@ struct MaxlocArgs {
   int32_t *partial_arg; // scratch leaf units of multi-block roots
   int32_t *counter;
   int32_t bs;
+  int32_t *status;      // the forest's device status word (a refused or timed-out stage)
 };
 
 template <typename T> __device__ __forceinline__ bool greater(T a, T b) { return a > b; }
@@ -1597,6 +1598,31 @@ template <> __device__ __forceinline__ bool greater<bf16>(bf16 a, bf16 b) {
   return __bfloat162float(a) > __bfloat162float(b);
 }
 
+// Single-leaf roots of a masked or pairs tile: the root element is its leaf's, and so is the
+// location.
+template <typename T> __device__ __forceinline__ void maxloc_single_tile(const MaxlocArgs &a, const RmTile &t) {
+  const T *leaf = static_cast<const T *>(a.leaf);
+  T *out = static_cast<T *>(a.out);
+  const int32_t bs = a.bs;
+  const int32_t work = t.cnt * bs;
+  for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+    const int32_t k = w / bs, c = w - k * bs;
+    int64_t ru, lu;
+    if (t.kind == T_MASKED) {
+      const int64_t bit = t.mask0 + t.k0 + k;
+      if (!((a.mask[bit >> 5] >> (bit & 31)) & 1u)) continue;
+      ru = t.root0 + t.k0 + k;
+      lu = t.leaf0 + t.k0 + k;
+    } else {
+      ru = a.pr_root[t.a + k];
+      lu = a.pr_leaf[t.a + k];
+    }
+    out[ru * bs + c] = leaf[lu * bs + c];
+    a.arg[ru * bs + c] = int32_t(lu);
+  }
+}
+
+// The general form (any unit): one thread per (block, element), walking the block's entries.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) maxloc_kernel(MaxlocArgs a) {
   const RmTile t = a.tiles[blockIdx.x];
@@ -1605,21 +1631,7 @@ __global__ void __launch_bounds__(kThreads) maxloc_kernel(MaxlocArgs a) {
   const int32_t bs = a.bs;
   const int32_t work = t.cnt * bs;
   if (t.kind == T_MASKED || t.kind == T_PAIRS) {
-    for (int32_t w = threadIdx.x; w < work; w += kThreads) {
-      const int32_t k = w / bs, c = w - k * bs;
-      int64_t ru, lu;
-      if (t.kind == T_MASKED) {
-        const int64_t bit = t.mask0 + t.k0 + k;
-        if (!((a.mask[bit >> 5] >> (bit & 31)) & 1u)) continue;
-        ru = t.root0 + t.k0 + k;
-        lu = t.leaf0 + t.k0 + k;
-      } else {
-        ru = a.pr_root[t.a + k];
-        lu = a.pr_leaf[t.a + k];
-      }
-      out[ru * bs + c] = leaf[lu * bs + c];
-      a.arg[ru * bs + c] = int32_t(lu);
-    }
+    maxloc_single_tile<T>(a, t);
   } else if (t.kind == T_CHUNKS) {
     for (int32_t w = threadIdx.x; w < work; w += kThreads) {
       const int32_t cl = w / bs, c = w - cl * bs;
@@ -1658,6 +1670,177 @@ __global__ void __launch_bounds__(kThreads) maxloc_kernel(MaxlocArgs a) {
         *ctr = 0;
       }
     }
+  }
+}
+
+// MAX with location, gather-then-fold (the one-vector-unit kernel's tile list and stage): a
+// fold tile's records and leaf entries come into shared memory by bulk copies, and its blocks go
+// in groups of (block, vector) items.  For each group the CTA copies rounds of whole leaf units
+// into shared memory by cp.async; each item keeps, per element of its vector, the running
+// maximum and the leaf unit of its first occurrence in canonical order (a strictly greater value
+// replaces it), carried across rounds.  A single-block root takes the item's result; the blocks
+// of a multi-block root leave partials (values and locations) whose last arrivers combine them
+// in two levels in block order -- super-blocks of FOLD_BLOCK blocks, then the root -- with the
+// same strict comparison, which keeps the earliest maximum: the serial definition's result.
+// MaxlocFlat::nv vectors of VB bytes make a unit of bs elements.
+struct MaxlocFlat {
+  int32_t nv;
+  uint32_t nv_m;   // DivMagic of nv
+  int32_t nv_s;
+};
+
+template <typename T, int VB>
+__device__ __forceinline__ void maxloc_store(const MaxlocArgs &a, int64_t e0, const Pack<T, VB> &v,
+                                             const int32_t (&loc)[Pack<T, VB>::L]) {
+  st<T, VB>(a.out, e0 / Pack<T, VB>::L, v);
+#pragma unroll
+  for (int l = 0; l < Pack<T, VB>::L; ++l) a.arg[e0 + l] = loc[l];
+}
+
+// Fold n partials (values and locations, stride bs elements) from slot `slot` into (v, loc)
+// in order, strictly greater replacing.
+template <typename T, int VB>
+__device__ __forceinline__ void maxloc_fold_partials(const MaxlocArgs &a, int64_t slot, int32_t n, int32_t c0,
+                                                     Pack<T, VB> &v, int32_t (&loc)[Pack<T, VB>::L]) {
+  constexpr int L = Pack<T, VB>::L;
+  const T *pv = static_cast<const T *>(a.partial);
+  for (int32_t i = 0; i < n; ++i) {
+    const int64_t e = (slot + i) * a.bs + c0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const T y = __ldcg(pv + e + l);
+      if (i == 0 || greater(y, v.v[l])) {
+        v.v[l] = y;
+        loc[l] = __ldcg(a.partial_arg + e + l);
+      }
+    }
+  }
+}
+
+template <typename T, int VB>
+__device__ __forceinline__ void maxloc_finish(const MaxlocArgs &a, const MaxlocFlat &f, const Block &b, int32_t vv,
+                                              Pack<T, VB> v, int32_t (&loc)[Pack<T, VB>::L]) {
+  constexpr int L = Pack<T, VB>::L;
+  const int32_t c0 = vv * L;                                  // the vector's first element in the unit
+  if (b.comb < 0) {
+    maxloc_store<T, VB>(a, int64_t(b.root) * a.bs + c0, v, loc);
+    return;
+  }
+  const Comb cb = a.combs[b.comb];
+  const int32_t ci = (b.e0 - cb.e_first) / FOLD_BLOCK;       // block index in the root
+  const int32_t sb = ci / FOLD_BLOCK;                         // super-block
+  const int32_t nsb = (cb.nch + FOLD_BLOCK - 1) / FOLD_BLOCK;
+  const int32_t in_sb = min(FOLD_BLOCK, cb.nch - sb * FOLD_BLOCK);
+  T *pv = static_cast<T *>(a.partial);
+  {
+    const int64_t e = (int64_t(cb.slot) + ci) * a.bs + c0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      __stcg(pv + e + l, v.v[l]);
+      __stcg(a.partial_arg + e + l, loc[l]);
+    }
+  }
+  __threadfence();
+  int32_t *ctr = a.counter + int64_t(cb.ctr + sb) * f.nv + vv;
+  if (atomicAdd(ctr, 1) != in_sb - 1) return;
+  __threadfence();
+  maxloc_fold_partials<T, VB>(a, int64_t(cb.slot) + sb * FOLD_BLOCK, in_sb, c0, v, loc);
+  *ctr = 0;   // ready for the next operation
+  if (nsb > 1) {
+    const int64_t e = (int64_t(cb.slot1) + sb) * a.bs + c0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      __stcg(pv + e + l, v.v[l]);
+      __stcg(a.partial_arg + e + l, loc[l]);
+    }
+    __threadfence();
+    int32_t *rctr = a.counter + int64_t(cb.ctr + nsb) * f.nv + vv;
+    if (atomicAdd(rctr, 1) != nsb - 1) return;
+    __threadfence();
+    maxloc_fold_partials<T, VB>(a, cb.slot1, nsb, c0, v, loc);
+    *rctr = 0;
+  }
+  maxloc_store<T, VB>(a, int64_t(cb.root) * a.bs + c0, v, loc);
+}
+
+template <typename T, int VB>
+__global__ void __launch_bounds__(kThreads, RM_NV1_BLOCKS) maxloc_flat_kernel(MaxlocArgs a, MaxlocFlat f) {
+  constexpr int L = Pack<T, VB>::L;
+  const RmTile t = a.tiles[blockIdx.x];
+  if (t.kind == T_MASKED || t.kind == T_PAIRS) {
+    maxloc_single_tile<T>(a, t);
+    return;
+  }
+  if (t.kind != T_CHUNKS) return;
+  __shared__ alignas(16) BlockRec s_rec[RM_STAGE_RECS];
+  __shared__ alignas(16) int32_t s_leaf[RM_STAGE_LEAVES_NV1];
+  __shared__ alignas(16) unsigned char s_raw[RM_FLAT_BYTES];
+  __shared__ alignas(8) uint64_t s_bar;
+  const int32_t r0 = t.a & ~1, r1 = (t.a + t.cnt + 2) & ~1;
+  const int32_t l0 = t.k0 & ~3, l1 = int32_t((t.e1 + 3) & ~int64_t(3));
+  if (t.cnt > RM_TILE_CHUNKS || r1 - r0 > RM_STAGE_RECS || l1 - l0 > RM_STAGE_LEAVES_NV1) {
+    if (threadIdx.x == 0 && a.status) atomicOr(a.status, DEVSTAT_TILE_REFUSED);
+    return;
+  }
+  const bool staged = stage2(s_rec, a.blocks + r0, uint32_t(r1 - r0) * uint32_t(sizeof(BlockRec)), s_leaf,
+                             a.m_leaf + l0, uint32_t(l1 - l0) * 4u, &s_bar, a.status);
+  if (!__syncthreads_and(staged)) return;
+  // (block, vector) items per thread: a 16-byte vector of 2-byte elements keeps eight
+  // locations, so one item
+  constexpr int NIT = VB >= 16 ? (L > 4 ? 1 : 2) : 4;
+  constexpr int R = RM_FLAT_BYTES / VB;                  // leaf vectors per round
+  const int32_t nv = f.nv;                               // 1 <= nv <= min(R, NIT * kThreads)
+  const int32_t gb = NIT * kThreads / nv, rl = R / nv;   // blocks per group, leaf units per round
+  const int32_t *idx = s_leaf + (t.k0 - l0);             // idx[i]: leaf unit of entry k0 + i
+  const BlockRec *rec = s_rec + (t.a - r0);
+  Pack<T, VB> *s_val = reinterpret_cast<Pack<T, VB> *>(s_raw);
+  const char *leaf = static_cast<const char *>(a.leaf);
+  for (int32_t g0 = 0; g0 < t.cnt; g0 += gb) {
+    const int32_t g1 = min(t.cnt, g0 + gb), nitems = (g1 - g0) * nv;
+    int32_t bw[NIT], vv[NIT];
+    Pack<T, VB> best[NIT];
+    int32_t loc[NIT][L];
+#pragma unroll
+    for (int j = 0; j < NIT; ++j) {
+      const int32_t it = threadIdx.x + j * kThreads;
+      bw[j] = -1;
+      if (it < nitems) {
+        const int32_t q = nv == 1 ? it : div_by(it, f.nv_m, f.nv_s);
+        bw[j] = g0 + q;
+        vv[j] = it - q * nv;
+      }
+    }
+    const int32_t e0 = int32_t(rec[g0].e0 - t.k0), e1 = int32_t(rec[g1].e0 - t.k0);
+    for (int32_t q0 = e0; q0 < e1; q0 += rl) {
+      const int32_t nq = min(rl, e1 - q0), nvec = nq * nv;
+      if (q0 > e0) __syncthreads();   // the previous round's vectors are folded
+      for (int32_t k = threadIdx.x; k < nvec; k += kThreads) {
+        const int32_t e = nv == 1 ? k : div_by(k, f.nv_m, f.nv_s), v = k - e * nv;
+        cp_async_vec<VB>(s_val + k, leaf + (int64_t(idx[q0 + e]) * nv + v) * VB);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NIT; ++j) {
+        if (bw[j] < 0) continue;
+        const int32_t b0 = int32_t(rec[bw[j]].e0 - t.k0), b1 = int32_t(rec[bw[j] + 1].e0 - t.k0);
+        const int32_t lo = max(b0, q0), hi = min(b1, q0 + nq);
+        for (int32_t i = lo; i < hi; ++i) {
+          const Pack<T, VB> y = s_val[(i - q0) * nv + vv[j]];
+          const int32_t lu = idx[i];
+#pragma unroll
+          for (int l = 0; l < L; ++l)
+            if (i == b0 || greater(y.v[l], best[j].v[l])) {
+              best[j].v[l] = y.v[l];
+              loc[j][l] = lu;
+            }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NIT; ++j)
+      if (bw[j] >= 0) maxloc_finish<T, VB>(a, f, load_block(rec, a.combs, bw[j]), vv[j], best[j], loc[j]);
+    __syncthreads();   // s_val is free for the next group
   }
 }
 

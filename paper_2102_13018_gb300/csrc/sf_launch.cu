@@ -114,13 +114,13 @@ cudaError_t launch_dg_bulk(int dtype, int op, int vb, const DgBulkArgs &b, cudaS
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, cudaStream_t s) {
+cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, int vb, const MaxlocFlat &f, cudaStream_t s) {
   switch (dtype) {
-    case SF_INT32: return launch_maxloc_t<int32_t>(a, ntiles, s);
-    case SF_INT64: return launch_maxloc_t<int64_t>(a, ntiles, s);
-    case SF_FP32: return launch_maxloc_t<float>(a, ntiles, s);
-    case SF_FP64: return launch_maxloc_t<double>(a, ntiles, s);
-    case SF_BF16: return launch_maxloc_t<bf16>(a, ntiles, s);
+    case SF_INT32: return launch_maxloc_t<int32_t>(a, ntiles, vb, f, s);
+    case SF_INT64: return launch_maxloc_t<int64_t>(a, ntiles, vb, f, s);
+    case SF_FP32: return launch_maxloc_t<float>(a, ntiles, vb, f, s);
+    case SF_FP64: return launch_maxloc_t<double>(a, ntiles, vb, f, s);
+    case SF_BF16: return launch_maxloc_t<bf16>(a, ntiles, vb, f, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -68,10 +68,11 @@ template <typename T> cudaError_t launch_dg_t(int op, int vb, const DgLaunch &L)
 template <typename T> cudaError_t launch_dg_bulk_t(int op, int vb, const DgBulkArgs &b, cudaStream_t s);
 
 // MAX with location and its gradient scatter (per dtype)
-cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, cudaStream_t s);
+cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, int vb, const MaxlocFlat &f, cudaStream_t s);
 cudaError_t launch_maxloc_scatter(int dtype, const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n,
                                   int32_t bs, cudaStream_t s);
-template <typename T> cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, cudaStream_t s);
+template <typename T>
+cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, int vb, const MaxlocFlat &f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n, int32_t bs,
                                     cudaStream_t s);

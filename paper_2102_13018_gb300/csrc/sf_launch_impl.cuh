@@ -196,10 +196,22 @@ cudaError_t launch_dg_t(int op, int vb, const DgLaunch &L) {
   return cudaErrorInvalidValue;
 }
 
+// vb == 0: the general kernel (any unit, a.tiles = rm_fold_tiles); vb = 4, 8 or 16 (at least the
+// element size): the gather-then-fold kernel on f.nv vectors of vb bytes (a.tiles =
+// rm_fold_nv1_tiles).
 template <typename T>
-cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, cudaStream_t s) {
+cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, int vb, const MaxlocFlat &f, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
-  maxloc_kernel<T><<<ntiles, kThreads, 0, s>>>(a);
+  if (vb == 0) {
+    maxloc_kernel<T><<<ntiles, kThreads, 0, s>>>(a);
+  } else if (vb == 16) {
+    maxloc_flat_kernel<T, 16><<<ntiles, kThreads, 0, s>>>(a, f);
+  } else if constexpr (sizeof(T) >= 4) {
+    if (vb != int(sizeof(T))) return cudaErrorInvalidValue;
+    maxloc_flat_kernel<T, int(sizeof(T))><<<ntiles, kThreads, 0, s>>>(a, f);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -219,7 +231,7 @@ cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, v
   template cudaError_t launch_ts_ops_t<T>(int, int, bool, bool, const TsLaunch &);                     \
   template cudaError_t launch_dg_t<T>(int, int, const DgLaunch &);                                     \
   template cudaError_t launch_dg_bulk_t<T>(int, int, const DgBulkArgs &, cudaStream_t);                \
-  template cudaError_t launch_maxloc_t<T>(const MaxlocArgs &, int, cudaStream_t);                      \
+  template cudaError_t launch_maxloc_t<T>(const MaxlocArgs &, int, int, const MaxlocFlat &, cudaStream_t);  \
   template cudaError_t launch_maxloc_scatter_t<T>(const int32_t *, const void *, void *, int64_t, int32_t, \
                                                   cudaStream_t);
 

@@ -1,7 +1,8 @@
-"""The gather-then-fold deterministic Reduce of multi-vector units (SUM/MIN/MAX with nv > 1
-vectors per unit) against the oracle, bit for bit (GB300): power-law and Zipf in-degrees, a
-heavy star whose fold runs three levels, units up to the kernel's vector limit and one past it
-(the general kernel), vector widths 4/8/16 bytes, and the Reduce from zero."""
+"""The gather-then-fold kernels against the oracle, bit for bit (GB300): the deterministic
+Reduce of multi-vector units (SUM/MIN/MAX with nv > 1 vectors per unit) and MAX with location
+(values and leaf locations, ties resolved by canonical order).  Power-law and Zipf in-degrees,
+a heavy star whose fold runs three levels, units up to the kernels' vector limits and past them
+(the general kernels), vector widths 4/8/16 bytes, and the Reduce from zero."""
 import numpy as np
 import pytest
 
@@ -100,3 +101,54 @@ def test_signed_zero_ties_multi_vector():
         r = to_dev(root, "fp64")
         sf.reduce(to_dev(leaf, "fp64"), r, op, bs=bs)
         assert_bits_equal(to_host(r, "fp64"), oracle.reduce(f, "fp64", bs, leaf, root, op), f"signed zeros {op}")
+
+
+# MAX with location (the autograd MAX forward): gather-then-fold for units of 4/8/16-byte
+# vectors, the general kernel otherwise; integer data in 0..999 makes ties on most roots, so the
+# first maximum in canonical order decides the location
+MAXLOC_UNITS = [("fp32", 64), ("bf16", 64), ("fp64", 2), ("int64", 3), ("bf16", 8), ("int32", 5), ("fp32", 1),
+                ("bf16", 3)]
+
+
+def _edge_leaves(f):
+    ro, lo = oracle.layout(f)
+    return np.concatenate([lo[q] + (np.arange(f.nleaves[q]) if f.ilocal[q] is None else np.asarray(f.ilocal[q]))
+                           for q in range(f.nranks)]).astype(np.int64)
+
+
+@pytest.mark.parametrize("f", FORESTS + [sfgen.zipf_forest(5, 3, 300000, 500, 4)], ids=lambda f: f.name)
+@pytest.mark.parametrize("dtype,bs", MAXLOC_UNITS)
+def test_maxloc_bit_exact(f, dtype, bs):
+    sf = StarForest.from_forest(f).setup() if f.name.startswith("zipf3") else sf_for(f)
+    _, leaf = make_data(f, dtype, bs, 1704)
+    want_v, want_e = oracle.reduce_maxloc(f, dtype, bs, leaf)
+    L = _edge_leaves(f)
+    ro, lo = oracle.layout(f)
+    root = to_dev(np.zeros(int(ro[-1]) * bs, oracle.NPTYPE[dtype]), dtype)
+    arg = torch.full((int(ro[-1]) * bs,), -1, dtype=torch.int32, device="cuda")
+    l = to_dev(leaf, dtype)
+    for call in range(2):   # the second call finds the arrival counters reset
+        sf.reduce_maxloc(l, root, arg, bs=bs)
+        assert_bits_equal(to_host(root, dtype), want_v, f"maxloc value {f.name} {dtype}x{bs} call {call}")
+        want_leaf = np.where(want_e >= 0, L[np.maximum(want_e, 0)], -1)
+        got = arg.cpu().numpy().astype(np.int64)
+        assert np.array_equal(got, want_leaf), f"maxloc location {f.name} {dtype}x{bs}: " \
+            f"{int((got != want_leaf).sum())} differ"
+    assert sf.device_status() == 0
+
+
+def test_maxloc_heavy_star_three_fold_levels():
+    n = 300000
+    f = sfgen.Forest(1, np.array([3]), np.array([n]), [None], [np.zeros(n, np.int32)],
+                     [(np.arange(n) % 7 == 0).astype(np.int64)], name="heavystar")
+    sf = StarForest.from_forest(f).setup()
+    L = _edge_leaves(f)
+    for dtype, bs in (("fp32", 8), ("int32", 4), ("bf16", 16)):
+        _, leaf = make_data(f, dtype, bs, 1705)
+        want_v, want_e = oracle.reduce_maxloc(f, dtype, bs, leaf)
+        root = to_dev(np.zeros(3 * bs, oracle.NPTYPE[dtype]), dtype)
+        arg = torch.full((3 * bs,), -1, dtype=torch.int32, device="cuda")
+        sf.reduce_maxloc(to_dev(leaf, dtype), root, arg, bs=bs)
+        assert_bits_equal(to_host(root, dtype), want_v, f"heavy star maxloc {dtype}x{bs}")
+        assert np.array_equal(arg.cpu().numpy().astype(np.int64), np.where(want_e >= 0, L[np.maximum(want_e, 0)], -1))
+    assert sf.device_status() == 0
