@@ -310,6 +310,14 @@ int sf_reduce_maxloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdat
 int sf_maxloc_scatter(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
                       sf_stream_t stream);
 
+/* The same gradient written whole: every connected leaf l of root r gets, per element c,
+ * leafgrad[l*bs + c] = rootgrad[r*bs + c] if argleaf[r*bs + c] == l, else 0 (argleaf as
+ * sf_reduce_maxloc wrote it).  Leaves with no root are not written, so a forest whose leaves
+ * are all connected needs no zero fill of leafgrad first.  Root-major: each leaf unit is
+ * written once, no leaf is read.  Same errors as sf_maxloc_scatter. */
+int sf_maxloc_grad(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
+                   sf_stream_t stream);
+
 /* ---- Batched execution (Sec. V.D: launch cost and pipelining; CUDA graphs as future work) ----
  * A batch runs many forests' operations with few kernel launches: operations are grouped by
  * kernel variant (element type, op, vector width, data path, Reduce mode) and each group is one

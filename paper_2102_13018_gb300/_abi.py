@@ -121,6 +121,7 @@ def load():
     for name in ("sf_gather_begin", "sf_gather_end", "sf_scatter_begin", "sf_scatter_end"):
         getattr(lib, name).argtypes = [vp, sf_unit, vp, vp, vp]
     lib.sf_maxloc_scatter.argtypes = [vp, sf_unit, vp, vp, vp, vp]
+    lib.sf_maxloc_grad.argtypes = [vp, sf_unit, vp, vp, vp, vp]
     lib.sf_batch_create.argtypes = [P(vp)]
     lib.sf_batch_run.argtypes = [vp, P(sf_batch_op), i32, i32, vp]
     lib.sf_batch_launches.argtypes = [vp, P(i32)]

@@ -83,8 +83,9 @@ class _ReduceMax(torch.autograd.Function):
     def backward(ctx, g):
         (arg,) = ctx.saved_tensors
         sf, bs = ctx.sf, ctx.bs
-        gleaf = torch.zeros(sf.leaf_extent, bs, dtype=g.dtype, device=g.device)
-        sf.maxloc_scatter(arg, g.contiguous(), gleaf, bs=bs)
+        # every connected leaf's unit is written (the selected elements of g, zeros elsewhere)
+        gleaf = _leaf_out(sf, bs, g)
+        sf.maxloc_grad(arg, g.contiguous(), gleaf, bs=bs)
         return gleaf, None
 
 

@@ -856,6 +856,30 @@ int sf_reduce_maxloc(sf_t *sf, sf_unit unit, const void *leafdata, void *rootdat
   return launched(launch_maxloc(unit.dtype, a, sf->dp.n_rm_fold_tiles, 0, f, s));
 }
 
+int sf_maxloc_grad(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
+                   sf_stream_t stream) {
+  int rc;
+  if ((rc = ensure_ready(sf)) || (rc = check_unit(unit, SF_MAX))) return rc;
+  const int w = elem_size(unit.dtype);
+  if (sf->info.nroots_total && ((rc = check_ptr(argleaf, 4)) || (rc = check_ptr(rootgrad, w)))) return rc;
+  if (sf->info.leaf_extent_total && (rc = check_ptr(leafgrad, w))) return rc;
+  if (sf->info.nedges == 0) return SF_SUCCESS;
+  const int ub = w * unit.bs;
+  const int vb = pick_vb(w, ub, true, {rootgrad, leafgrad}) == 16 ? 16 : w;
+  MaxlocArgs a{};
+  a.mask = sf->dp.mask;
+  a.pr_root = sf->dp.pr_root;
+  a.pr_leaf = sf->dp.pr_leaf;
+  a.m_leaf = sf->dp.m_leaf;
+  a.blocks = sf->dp.blocks;
+  a.combs = sf->dp.combs;
+  a.tiles = sf->dp.rm_fold_tiles;
+  a.arg = const_cast<int32_t *>(argleaf);
+  a.bs = unit.bs;
+  return launched(launch_maxloc_grad(unit.dtype, a, sf->dp.n_rm_fold_tiles, vb, ub / vb, rootgrad, leafgrad,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
 int sf_maxloc_scatter(sf_t *sf, sf_unit unit, const int32_t *argleaf, const void *rootgrad, void *leafgrad,
                       sf_stream_t stream) {
   int rc;

@@ -1844,6 +1844,50 @@ __global__ void __launch_bounds__(kThreads, RM_NV1_BLOCKS) maxloc_flat_kernel(Ma
   }
 }
 
+// The gradient of MAX with location, written leaf by leaf in root-major order: every connected
+// leaf l of root r gets, per element c, grad_root[r, c] if arg[r, c] == l and 0 otherwise (whole
+// units, no read of the leaves, no combine across blocks).  Single-leaf roots are their leaf's
+// maximum, so their leaves get grad_root[r] whole.  Leaves without a root are not written.
+// nv vectors of VB bytes make a unit of bs elements; a.tiles is rm_fold_tiles.
+template <typename T, int VB>
+__global__ void __launch_bounds__(kThreads) maxloc_grad_kernel(MaxlocArgs a, int32_t nv, uint32_t nv_m, int32_t nv_s,
+                                                               const void *grad_root, void *grad_leaf) {
+  constexpr int L = Pack<T, VB>::L;
+  const RmTile t = a.tiles[blockIdx.x];
+  const int32_t work = t.cnt * nv;
+  for (int32_t w = threadIdx.x; w < work; w += kThreads) {
+    const int32_t k = nv == 1 ? w : div_by(w, nv_m, nv_s), v = w - k * nv;
+    if (t.kind == T_MASKED || t.kind == T_PAIRS) {
+      int64_t ru, lu;
+      if (t.kind == T_MASKED) {
+        const int64_t bit = t.mask0 + t.k0 + k;
+        if (!((__ldg(a.mask + (bit >> 5)) >> (bit & 31)) & 1u)) continue;
+        ru = t.root0 + t.k0 + k;
+        lu = t.leaf0 + t.k0 + k;
+      } else {
+        ru = __ldg(a.pr_root + t.a + k);
+        lu = __ldg(a.pr_leaf + t.a + k);
+      }
+      st<T, VB>(grad_leaf, lu * nv + v, ld<T, VB>(grad_root, ru * nv + v));
+    } else if (t.kind == T_CHUNKS) {
+      const Block b = load_block(a.blocks, a.combs, t.a + k);
+      const Pack<T, VB> g = ld<T, VB>(grad_root, int64_t(b.root) * nv + v);
+      int32_t loc[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) loc[l] = __ldg(a.arg + int64_t(b.root) * a.bs + v * L + l);
+      for (int32_t e = 0; e < b.n; ++e) {
+        const int32_t lu = __ldg(a.m_leaf + b.e0 + e);
+        Pack<T, VB> o;
+        memset(&o, 0, sizeof o);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+          if (loc[l] == lu) o.v[l] = g.v[l];
+        st<T, VB>(grad_leaf, int64_t(lu) * nv + v, o);
+      }
+    }
+  }
+}
+
 // grad_leaf[arg[i] * bs + c] = grad_root[i] for every root element i = r * bs + c with arg >= 0
 // (each leaf belongs to one root, so no two elements write the same place).
 template <typename T>

@@ -125,6 +125,18 @@ cudaError_t launch_maxloc(int dtype, const MaxlocArgs &a, int ntiles, int vb, co
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_maxloc_grad(int dtype, const MaxlocArgs &a, int ntiles, int vb, int32_t nv, const void *grad_root,
+                               void *grad_leaf, cudaStream_t s) {
+  switch (dtype) {
+    case SF_INT32: return launch_maxloc_grad_t<int32_t>(a, ntiles, vb, nv, grad_root, grad_leaf, s);
+    case SF_INT64: return launch_maxloc_grad_t<int64_t>(a, ntiles, vb, nv, grad_root, grad_leaf, s);
+    case SF_FP32: return launch_maxloc_grad_t<float>(a, ntiles, vb, nv, grad_root, grad_leaf, s);
+    case SF_FP64: return launch_maxloc_grad_t<double>(a, ntiles, vb, nv, grad_root, grad_leaf, s);
+    case SF_BF16: return launch_maxloc_grad_t<bf16>(a, ntiles, vb, nv, grad_root, grad_leaf, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_maxloc_scatter(int dtype, const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n,
                                   int32_t bs, cudaStream_t s) {
   switch (dtype) {

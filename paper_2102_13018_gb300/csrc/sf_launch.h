@@ -73,6 +73,11 @@ cudaError_t launch_maxloc_scatter(int dtype, const int32_t *arg, const void *gra
                                   int32_t bs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, int vb, const MaxlocFlat &f, cudaStream_t s);
+cudaError_t launch_maxloc_grad(int dtype, const MaxlocArgs &a, int ntiles, int vb, int32_t nv, const void *grad_root,
+                               void *grad_leaf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_maxloc_grad_t(const MaxlocArgs &a, int ntiles, int vb, int32_t nv, const void *grad_root,
+                                 void *grad_leaf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n, int32_t bs,
                                     cudaStream_t s);

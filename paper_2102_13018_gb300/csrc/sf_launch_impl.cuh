@@ -216,6 +216,20 @@ cudaError_t launch_maxloc_t(const MaxlocArgs &a, int ntiles, int vb, const Maxlo
 }
 
 template <typename T>
+cudaError_t launch_maxloc_grad_t(const MaxlocArgs &a, int ntiles, int vb, int32_t nv, const void *grad_root,
+                                 void *grad_leaf, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const DivMagic dm = div_magic(uint32_t(nv));
+  if (vb == 16)
+    maxloc_grad_kernel<T, 16><<<ntiles, kThreads, 0, s>>>(a, nv, dm.m, dm.s, grad_root, grad_leaf);
+  else if (vb == int(sizeof(T)))
+    maxloc_grad_kernel<T, int(sizeof(T))><<<ntiles, kThreads, 0, s>>>(a, nv, dm.m, dm.s, grad_root, grad_leaf);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, void *grad_leaf, int64_t n, int32_t bs,
                                     cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -232,6 +246,8 @@ cudaError_t launch_maxloc_scatter_t(const int32_t *arg, const void *grad_root, v
   template cudaError_t launch_dg_t<T>(int, int, const DgLaunch &);                                     \
   template cudaError_t launch_dg_bulk_t<T>(int, int, const DgBulkArgs &, cudaStream_t);                \
   template cudaError_t launch_maxloc_t<T>(const MaxlocArgs &, int, int, const MaxlocFlat &, cudaStream_t);  \
+  template cudaError_t launch_maxloc_grad_t<T>(const MaxlocArgs &, int, int, int32_t, const void *, void *,    \
+                                               cudaStream_t);                                                 \
   template cudaError_t launch_maxloc_scatter_t<T>(const int32_t *, const void *, void *, int64_t, int32_t, \
                                                   cudaStream_t);
 

@@ -388,6 +388,13 @@ class StarForest:
                                           self._stream(stream)), "sf_maxloc_scatter")
         return leafgrad
 
+    def maxloc_grad(self, argleaf, rootgrad, leafgrad, bs=None, stream=None):
+        """Every connected leaf's gradient unit: rootgrad where argleaf names the leaf, else 0."""
+        u = self._unit(rootgrad, self.nroots_total, bs)
+        check(self._lib.sf_maxloc_grad(self._h, u, self._ptr(argleaf), self._ptr(rootgrad), self._ptr(leafgrad),
+                                       self._stream(stream)), "sf_maxloc_grad")
+        return leafgrad
+
     # ---------------------------------------------------------------- autotuner
     def autotune(self, kind: str, src, dst, op: str, bs=None, reps: int = 3, stream=None) -> str:
         """Time the Bcast variants (kind "bcast": path x vector width x tile size) or the Reduce

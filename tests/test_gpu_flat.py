@@ -152,3 +152,25 @@ def test_maxloc_heavy_star_three_fold_levels():
         assert_bits_equal(to_host(root, dtype), want_v, f"heavy star maxloc {dtype}x{bs}")
         assert np.array_equal(arg.cpu().numpy().astype(np.int64), np.where(want_e >= 0, L[np.maximum(want_e, 0)], -1))
     assert sf.device_status() == 0
+
+
+@pytest.mark.parametrize("f", FORESTS, ids=lambda f: f.name)
+@pytest.mark.parametrize("dtype,bs", [("fp32", 64), ("bf16", 64), ("fp64", 2), ("int32", 5), ("bf16", 3), ("fp32", 1)])
+def test_maxloc_grad_writes_every_connected_leaf(f, dtype, bs):
+    """The MAX backward: each connected leaf's unit becomes the root gradient where the oracle's
+    location names that leaf and 0 elsewhere; leaves without a root keep what they held."""
+    sf = sf_for(f)
+    _, leaf = make_data(f, dtype, bs, 1706)
+    _, want_e = oracle.reduce_maxloc(f, dtype, bs, leaf)
+    L = _edge_leaves(f)
+    argleaf = np.where(want_e >= 0, L[np.maximum(want_e, 0)], -1).astype(np.int32)
+    ro, lo = oracle.layout(f)
+    g = sfgen.data(dtype, int(ro[-1]) * bs, 1706, 3)
+    held = sfgen.data(dtype, int(lo[-1]) * bs, 1706, 4)
+    want = held.copy().reshape(-1, bs)
+    want[L] = 0
+    r, c = np.nonzero(argleaf.reshape(-1, bs) >= 0)
+    want[argleaf.reshape(-1, bs)[r, c], c] = g.reshape(-1, bs)[r, c]
+    out = to_dev(held, dtype)
+    sf.maxloc_grad(torch.from_numpy(argleaf).cuda(), to_dev(g, dtype), out, bs=bs)
+    assert_bits_equal(to_host(out, dtype), want.ravel(), f"maxloc grad {f.name} {dtype}x{bs}")
