@@ -59,7 +59,7 @@ struct sf_batch_s {
   cudaStream_t capture_stream = nullptr;
   // the variant groups of a stage are independent: they run side by side on these streams,
   // forked from and joined back into the caller's stream (parallel branches in the graph)
-  static constexpr int kLanes = 4;
+  static constexpr int kLanes = 8;
   cudaStream_t lanes[kLanes] = {};
   cudaEvent_t fork = nullptr, join[kLanes] = {};
 };
@@ -253,7 +253,8 @@ int ensure_lanes(sf_batch_t *b) {
 
 // Stage by stage (the groups are sorted by stage): a stage of one group runs on `s`; the groups
 // of a larger stage go to the lanes, largest first onto the least loaded lane (by tiles), and
-// `s` waits for every lane used before the next stage.
+// `s` waits for every lane used before the next stage.  On the 512-forest batch 8 lanes replay
+// 3% faster than 4, and 4 were 21% faster than one stream.
 int launch_groups(sf_batch_t *b, cudaStream_t s) {
   int rc;
   const size_t ng = b->groups.size();
