@@ -285,3 +285,31 @@ def test_diagonal_chunks_cover_the_spmv_scatter_and_leave_corner_cases_to_the_re
     # roots without an owned leaf, roots of the shuffled rank and roots of more than 64 leaves
     assert mix["dg_rest_roots"] > 0 and mix["dg_list_roots"] > 0
     assert 0 < mix["dg_roots"] < mix["connected_roots"]
+
+
+def test_tuning_knobs_validate_and_report_before_setup():
+    """The launch-shape and plan setters check their arguments; before the setup pass builds a
+    diagonal-chunk plan a forest reports the root-major Reduce plan whatever is selected."""
+    lib = _abi.load()
+    sf = StarForest.from_forest(sfgen.fig2())
+    for bad in (-1, 4, 99):
+        assert lib.sf_set_reduce_plan(sf._h, bad) == _abi.CODES["SF_ERR_ARG"]
+    for bad in (1, 3, 32):
+        assert lib.sf_set_vector_bytes(sf._h, bad) == _abi.CODES["SF_ERR_ARG"]
+    assert lib.sf_set_reduce_plan(None, 0) == _abi.CODES["SF_ERR_NULL"]
+    for plan in ("auto", "root_major", "diagonal", "diagonal_staged"):
+        t = sf.set_reduce_plan(plan).tuning()
+        assert t["reduce_plan"] == "root_major"
+        assert t["path"] == "fused" and t["mode"] == "deterministic" and t["vector_bytes"] == 0
+    sf.set_vector_bytes(8)
+    assert sf.tuning()["vector_bytes"] == 8
+
+
+def test_header_enums_match_the_binding():
+    import re
+    text = open(_abi.HEADER).read()
+    for prefix in ("SF_PLAN_", "SF_PATH_", "SF_MODE_"):
+        found = dict(re.findall(r"\b(" + prefix + r"[A-Z_]+)\s*=\s*(\d+)", text))
+        assert found, prefix
+        for name, val in found.items():
+            assert getattr(_abi, name) == int(val), name
