@@ -39,6 +39,10 @@ MUTANTS = {
     "edge_root_rank_ignored": ("R[e] = ro[f->rrank[e]] + f->rindex[e];", "R[e] = f->rindex[e];"),
     "gather_slots_reversed": ("  for (int64_t e = 0; e < E; ++e) slot[e] = first[R[e]]++;",
                               "  for (int64_t e = E - 1; e >= 0; --e) slot[e] = first[R[e]]++;"),
+    "maxloc_last_tie_wins": ("if (argedge[u] < 0 || less_than(dtype, (char *)out + u * w, src)) {",
+                             "if (argedge[u] < 0 || !less_than(dtype, src, (char *)out + u * w)) {"),
+    "maxloc_component_dropped": ("const char *src = (const char *)leafdata + (L[e] * bs + c) * w;",
+                                 "const char *src = (const char *)leafdata + (L[e] * bs) * w;"),
     "gather_slot_excludes_own_root": ("for (int64_t r = 0; r < NR; ++r) first[r + 1] += first[r];     /* edges",
                                       "for (int64_t r = 1; r < NR; ++r) first[r + 1] += first[r - 1];     /* edges"),
 }
@@ -119,6 +123,20 @@ def battery(lib):
         check("fig2_scatter", sc.tolist() == [106, 103, 104, 102, 108, 100, -1, 109, 101, 105, 107])
     except Exception:
         fails.append("gather_crash")
+    # MAX with location, two components with many ties: the first canonical edge per element
+    ym = (sfgen.data("int32", nl * 2, 13, 1) % 3).astype(np.int32)
+    vm, am = oracle.reduce_maxloc(fr, "int32", 2, ym, lib=lib)
+    ok = True
+    for c in range(2):
+        kc = ym.reshape(-1, 2)[:, c]
+        e_ = np.arange(len(L))
+        order = np.lexsort((e_, -kc[L].astype(np.int64), R))
+        first = np.ones(len(order), bool)
+        first[1:] = R[order][1:] != R[order][:-1]
+        want = np.full(nr, -1, np.int64)
+        want[R[order][first]] = e_[order][first]
+        ok &= np.array_equal(am.reshape(-1, 2)[:, c], want)
+    check("maxloc_first_tie", ok)
     # bf16 rounding tie
     t = np.array([0x3F808000, 0x3F818000], np.uint32).view(np.float32)
     check("bf16_tie", oracle.f32_to_bf16(t, lib=lib).tolist() == [0x3F80, 0x3F82])

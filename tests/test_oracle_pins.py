@@ -351,6 +351,41 @@ def test_maxloc_matches_lexsort():
     assert np.array_equal(val, want_val) and np.array_equal(arg, want_arg)
 
 
+@pytest.mark.parametrize("dtype,bs", [("fp64", 3), ("bf16", 2), ("int64", 4)])
+def test_maxloc_per_component_matches_lexsort(dtype, bs):
+    """MAX with location element by element of multi-component units: per (root, component)
+    the largest value and the first canonical edge holding it, from a numpy lexsort (bf16
+    compared as the float32 values of its bit patterns).  Values on a coarse grid tie often."""
+    f = sfgen.random_forest(23, 3, 10, 40)
+    L, R = npref.edge_arrays(f)
+    ro, lo = npref.offsets(f)
+    y = sfgen.data(dtype, lo[-1] * bs, 24, 1)
+    if dtype == "bf16":
+        y = (y & np.uint16(0xFE00)) | np.uint16(0x3C00)   # few distinct values: ties
+        key = (y.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    elif dtype == "fp64":
+        y = np.round(y * 4) / 4
+        key = y
+    else:
+        y = y % 7
+        key = y.astype(np.float64)
+    val, arg = oracle.reduce_maxloc(f, dtype, bs, y)
+    e = np.arange(len(L))
+    for c in range(bs):
+        kc = key.reshape(-1, bs)[:, c]
+        order = np.lexsort((e, -kc[L], R))      # by root, value descending, edge ascending
+        first = np.ones(len(order), bool)
+        first[1:] = R[order][1:] != R[order][:-1]
+        want_arg = np.full(ro[-1], -1, np.int64)
+        want_arg[R[order][first]] = e[order][first]
+        got_arg = arg.reshape(-1, bs)[:, c]
+        assert np.array_equal(got_arg, want_arg), f"component {c}"
+        has = want_arg >= 0
+        got_val = val.reshape(-1, bs)[:, c]
+        assert np.array_equal(got_val[has], y.reshape(-1, bs)[L[want_arg[has]], c])
+        assert not got_val[~has].any()
+
+
 def test_empty_forest_and_isolated():
     f = sfgen.Forest(2, np.array([3, 0]), np.array([0, 0]), [None, None],
                      [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int64)] * 2)
