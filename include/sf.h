@@ -88,10 +88,11 @@ enum { SF_PATH_AUTO = 0, SF_PATH_FUSED = 1, SF_PATH_THREE_PHASE = 2, SF_PATH_ROO
 
 /* Plans of the deterministic Reduce of one-vector units (SUM/MIN/MAX; results are identical):
  * ROOT_MAJOR: CSR-by-root fold tiles with a two-level combine for roots that span tiles.
- * DIAGONAL: 32-root chunks whose roots take their first leaf at one common offset (Sec. V.B's
- *   contiguous patterns, per chunk), then the root-major plan of the roots left out; only on
- *   forests where the setup pass found such chunks (sf_info.dg_chunks > 0).
- * DIAGONAL_STAGED: DIAGONAL with each tile's spans staged in shared memory by bulk copies.
+ * DIAGONAL: 32-root chunks whose roots each own a leaf at one common offset from the root
+ *   (Sec. V.B's contiguous patterns, per chunk), then the root-major plan of the roots left
+ *   out; only on forests where the setup pass found such chunks (sf_info.dg_chunks > 0).
+ * DIAGONAL_STAGED: DIAGONAL with each tile's spans staged in shared memory by bulk copies
+ *   (a single forest's Reduce; in a batch it runs as DIAGONAL).
  * AUTO: ROOT_MAJOR, or what sf_autotune measured fastest. */
 enum { SF_PLAN_AUTO = 0, SF_PLAN_ROOT_MAJOR = 1, SF_PLAN_DIAGONAL = 2, SF_PLAN_DIAGONAL_STAGED = 3 };
 
@@ -350,15 +351,17 @@ int sf_batch_run(sf_batch_t *batch, const sf_batch_op ops[], int32_t n, int32_t 
 int sf_batch_launches(const sf_batch_t *batch, int32_t *launches);
 int sf_batch_destroy(sf_batch_t *batch);
 
-/* Autotuner: times the variants of Bcast (kind SF_OP_BCAST: data path x vector width x two-sided
- * tile size) or of Reduce (kind SF_OP_REDUCE: mode x vector width, the plan for the
- * deterministic mode and the tile size for the atomic mode) on this forest, unit and op, `reps` times after one warm-up, writing into a
- * scratch copy of dst (src and dst are not modified), and keeps the fastest: its path or mode
- * becomes what SF_PATH_AUTO / SF_MODE_AUTO mean for the forest, its vector width and tile size
- * are set (sf_set_vector_bytes, sf_set_tile_edges).  *choice (may be NULL) receives the path or
- * mode; sf_get_tuning gives the rest, and a tuned plan becomes what SF_PLAN_AUTO means.  Allocates and synchronises.  Choosing SF_MODE_ATOMIC
- * trades bit-reproducibility for speed; pass SF_MODE_DETERMINISTIC as the forest's mode before
- * tuning, and the Reduce keeps it (only the vector width is tuned). */
+/* Autotuner: times the variants of Bcast (kind SF_OP_BCAST: data path x vector width x
+ * two-sided tile size) or of Reduce (kind SF_OP_REDUCE: mode x vector width, the plan for the
+ * deterministic mode and the tile size for the atomic mode) on this forest, unit and op,
+ * `reps` times after one warm-up, writing into a scratch copy of dst (src and dst are not
+ * modified), and keeps the fastest: its path or mode becomes what SF_PATH_AUTO / SF_MODE_AUTO
+ * mean for the forest, a tuned plan what SF_PLAN_AUTO means (when the forest's plan is AUTO),
+ * and its vector width and tile size are set (sf_set_vector_bytes, sf_set_tile_edges).
+ * *choice (may be NULL) receives the path or mode; sf_get_tuning gives the rest.  Allocates
+ * and synchronises.  Choosing SF_MODE_ATOMIC trades bit-reproducibility for speed; pass
+ * SF_MODE_DETERMINISTIC as the forest's mode before tuning, and the Reduce keeps it (then only
+ * the plan and the vector width are tuned). */
 int sf_autotune(sf_t *sf, sf_unit unit, int32_t kind, const void *src, void *dst, int32_t op, int32_t reps,
                 sf_stream_t stream, int32_t *choice);
 
